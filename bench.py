@@ -1,0 +1,378 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the Kalman-filter track-building path on one GB300.
+
+One step = the whole path on one CMS-like event (38 surfaces, 5000 tracks,
+~85k hits with 20 % noise, 6 candidates per seed): hit binning -> combinatorial
+building with duplicate removal -> forward fit of every found track (with
+per-layer checkpoints) -> adjoint of that fit -> backward fit.  Inputs are
+synthetic (seeded), generated on the host and resident in HBM before the timed
+region; the L2 is flushed between timed steps (inputs are smaller than L2).
+
+Metric: candidate Kalman steps per second (one step = one candidate
+propagated to one surface with all its chi2 evaluations and its update),
+counted by the kernel itself; events/s and fitted tracks/s are reported beside.
+
+Multi-GPU (torchrun): events are independent, each rank builds its own event
+(weak scaling), no collective on the data path; the max over ranks of the
+timed region is reported.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "C2 CMS-like event: 38 surfaces (14 barrel + 24 disk), 5000 tracks, ~85k hits incl. 20% noise, " \
+           "6 candidates/seed, chi2<30, then refit (fwd + adjoint + bwd) of every found track"
+METRIC = "candidate Kalman steps/s"
+UNIT = "cand-steps/s"
+
+# FP32 work per unit, counted from the kernel formulas (FMA = 2, add/mul = 1;
+# sqrt, rcp, sin/cos, atan, log counted separately as SFU): see the design doc
+FLOPS_NAV_TEST = 50       # one surface tested by the navigation (path + acceptance)
+FLOPS_CAND_STEP = 480     # propagate + Jacobian + J C J^T + material + window
+FLOPS_CHI2 = 32           # one candidate-hit chi2
+FLOPS_UPDATE = 198        # one Kalman update of a kept child
+FP32_LANES = 128          # per SM (Blackwell)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="mkf", choices=["mkf", "reference"])
+    ap.add_argument("--cpu-sample-seeds", type=int, default=0,
+                    help="seeds per oracle sample (0: sized for ~15 s of CPU work)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# oracle (CPU) timing: used by the cpu_baseline field and by --impl reference
+_EV = None
+
+
+def _worker_init():
+    global _EV
+    sys.path.insert(0, ROOT)
+    import synth
+    _EV = synth.make_config_event(2)
+
+
+def _worker_build(seeds):
+    import oracle
+    import numpy as np
+    ev = _EV
+    t0 = time.perf_counter()
+    out = oracle.build_event(oracle.Geo.of(ev.geom), ev.hit_xyz, ev.hit_lcov, ev.hit_layer, ev.seed_par[seeds],
+                             ev.seed_cov[seeds], chi2_cut=30.0, max_cands=6, max_holes=3, min_hits=4, dup_frac=0.5,
+                             dedup=False)
+    return out["stats"]["cand_steps"], time.perf_counter() - t0, int(np.asarray(seeds).size)
+
+
+def oracle_pool(n_workers):
+    import multiprocessing as mp
+    import oracle
+    oracle.build()   # compile once before the workers load it
+    ctx = mp.get_context("spawn")
+    return ctx.Pool(n_workers, initializer=_worker_init)
+
+
+def oracle_step(pool, n_workers, n_seeds, offset):
+    """Oracle building of n_seeds seeds of the event (spread over the pool)."""
+    import numpy as np
+    seeds = (offset + np.arange(n_seeds)) % 5000
+    chunks = [c for c in np.array_split(seeds, n_workers) if c.size]
+    t0 = time.perf_counter()
+    res = pool.map(_worker_build, chunks)
+    dt = time.perf_counter() - t0
+    return sum(r[0] for r in res), dt
+
+
+def n_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    """The reference arm: the FP64 oracle as it stands, on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cores = n_cores()
+    pool = oracle_pool(cores)
+    per_step = args.cpu_sample_seeds or 24 * cores
+    for w in range(args.warmup):
+        oracle_step(pool, cores, max(cores, per_step // 4), 1000 * w)
+    units = 0
+    elapsed = 0.0
+    for k in range(args.steps):
+        u, dt = oracle_step(pool, cores, per_step, 97 * k)
+        units += u
+        elapsed += dt
+    pool.close()
+    value = units / elapsed
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "%d seeds of the event per step" % per_step},
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d seeds x %d steps of the 5000-seed event, brute-force hit search, "
+                                       "one process per core" % (per_step, args.steps)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+
+    import synth
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+    import paper_2002_06295_gb300 as mkf
+
+    # CPU baseline first (spawned workers, before any heavy GPU work)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = n_cores()
+        pool = oracle_pool(cores)
+        per = args.cpu_sample_seeds or 40 * cores
+        u, dt = oracle_step(pool, cores, per, 0)
+        pool.close()
+        cpu = {"value": u / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "%d of the 5000 seeds of the C2 event (building only, brute-force hit search), "
+                         "one process per core, %.1f s" % (per, dt)}
+
+    dev = torch.device("cuda", local)
+    ev = synth.make_config_event(2, rank)
+    g = ev.geom
+    ctx = mkf.Context(local)
+    mkf.mkf_load_geometry(ctx, g.table(), g.bz, 64, 16)
+    mkf.mkf_set_timing(ctx, True)
+    spec = synth.CONFIGS[2]
+    f32 = dict(dtype=torch.float32)
+    host = dict(xyz=torch.tensor(ev.hit_xyz.T.copy(), **f32), lcov=torch.tensor(ev.hit_lcov.T.copy(), **f32),
+                layer=torch.tensor(ev.hit_layer, dtype=torch.int32),
+                hoff=torch.tensor([0, ev.n_hits], dtype=torch.int64),
+                sp=torch.tensor(ev.seed_par.T.copy(), **f32), sc=torch.tensor(ev.seed_cov.T.copy(), **f32),
+                soff=torch.tensor([0, ev.n_seeds], dtype=torch.int64))
+    host = {k: v.pin_memory() for k, v in host.items()}
+    d = {k: v.to(dev) for k, v in host.items()}
+    S, L = ev.n_seeds, g.n_layers
+    out = mkf.alloc_build_outputs(ctx, S)
+    ckpt = torch.empty((L, 27, S), dtype=torch.float32, device=dev)
+    fit_out = dict(par=torch.empty((6, S), device=dev), cov=torch.empty((21, S), device=dev),
+                   chi2=torch.empty(S, device=dev), ok=torch.empty(S, dtype=torch.int32, device=dev))
+    bwd_out = dict(par=torch.empty((6, S), device=dev), cov=torch.empty((21, S), device=dev),
+                   chi2=torch.empty(S, device=dev), ok=torch.empty(S, dtype=torch.int32, device=dev))
+    g_chi2 = torch.ones(S, device=dev)
+    adj_out = dict(g_hit=torch.empty((3, ev.n_hits), device=dev), g_align=torch.empty((L, 3), device=dev),
+                   g_x0=torch.empty(L, device=dev))
+    has_adjoint = [True]
+    stream = torch.cuda.current_stream()
+
+    def step(inp):
+        mkf.mkf_bin_hits(ctx, inp["xyz"], inp["lcov"], inp["layer"], inp["hoff"])
+        mkf.mkf_build_tracks(ctx, inp["sp"], inp["sc"], inp["soff"], chi2_cut=spec["chi2_cut"],
+                             max_cands=spec["max_cands"], max_holes=spec["max_holes"], min_hits=spec["min_hits"],
+                             dup_frac=spec["dup_frac"], out=out)
+        mkf.mkf_fit_tracks(ctx, inp["xyz"], inp["lcov"], inp["layer"], out["hits"], inp["sp"], inp["sc"],
+                           ckpt=ckpt, out=fit_out)
+        if has_adjoint[0]:
+            try:
+                mkf.mkf_fit_tracks_adjoint(ctx, inp["xyz"], inp["lcov"], inp["layer"], out["hits"], inp["sp"],
+                                           inp["sc"], ckpt, g_chi2=g_chi2, out=adj_out)
+            except mkf.MkfError:
+                has_adjoint[0] = False
+        mkf.mkf_fit_backward(ctx, inp["xyz"], inp["lcov"], inp["layer"], out["hits"], fit_out["par"], out=bwd_out)
+
+    # warm-up
+    for _ in range(max(args.warmup, 3) if args.warmup > 0 else 0):
+        step(d)
+    torch.cuda.synchronize()
+    mkf.mkf_sync(ctx)
+    stats = mkf.mkf_get_stats(ctx)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    build_ms, bin_ms, fit_ms, adj_ms, bwd_ms, dd_ms = [], [], [], [], [], []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        evs[k][0].record(stream)
+        step(d)
+        evs[k][1].record(stream)
+        tm = mkf.mkf_get_timings(ctx)
+        build_ms.append(tm["build"]); bin_ms.append(tm["bin"]); fit_ms.append(tm["fit"])
+        adj_ms.append(tm["adjoint"]); bwd_ms.append(tm["backward"]); dd_ms.append(tm["dedup"])
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    # end to end through the API with host buffers: H2D inputs, path, D2H results
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    res_host = dict(hits=torch.empty_like(out["hits"], device="cpu").pin_memory(),
+                    par=torch.empty_like(fit_out["par"], device="cpu").pin_memory(),
+                    flags=torch.empty_like(out["flags"], device="cpu").pin_memory(),
+                    chi2=torch.empty_like(fit_out["chi2"], device="cpu").pin_memory())
+    d2h = sum(v.numel() * v.element_size() for v in res_host.values())
+    e2e_ms = []
+    dd = {k: torch.empty_like(v) for k, v in d.items()}
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for kk, v in host.items():
+            dd[kk].copy_(v, non_blocking=True)
+        step(dd)
+        res_host["hits"].copy_(out["hits"], non_blocking=True)
+        res_host["par"].copy_(fit_out["par"], non_blocking=True)
+        res_host["flags"].copy_(out["flags"], non_blocking=True)
+        res_host["chi2"].copy_(fit_out["chi2"], non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    mkf.mkf_sync(ctx)
+
+    if rank != 0:
+        return
+    units = stats["cand_steps"] * world
+    value = units * args.steps / (total_ms * 1e-3)
+    e2e_value = units * args.steps / (sum(e2e_ms) * 1e-3)
+    b_ms = statistics.mean(build_ms)
+    alg_flops = (stats["nav_tests"] * FLOPS_NAV_TEST + stats["cand_steps"] * FLOPS_CAND_STEP
+                 + stats["chi2_evals"] * FLOPS_CHI2 + stats["updates"] * FLOPS_UPDATE)
+    achieved = alg_flops / (b_ms * 1e-3) / 1e12
+    props = torch.cuda.get_device_properties(dev)
+    max_mhz = clk.get("sm_max_mhz") or measured_peaks().get("sm_max_mhz", 2070.0)
+    peak = props.multi_processor_count * FP32_LANES * 2 * max_mhz * 1e6 / 1e12
+    launches_per_step = 6 + 1 + 3 + 1 + (1 if has_adjoint[0] else 0) + 1
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "events_per_step_per_gpu": 1, "tracks": S, "hits": ev.n_hits,
+                   "surfaces": L, "max_cands": spec["max_cands"], "l2": "flushed (256 MB write) between timed steps",
+                   "adjoint_in_step": has_adjoint[0]},
+        "events_per_s": world * args.steps / (total_ms * 1e-3),
+        "fit_tracks_per_s": world * S * args.steps / (total_ms * 1e-3),
+        "stage_ms": {"bin": statistics.mean(bin_ms), "build": b_ms, "dedup": statistics.mean(dd_ms),
+                     "fit": statistics.mean(fit_ms), "adjoint": statistics.mean(adj_ms) if has_adjoint[0] else None,
+                     "backward": statistics.mean(bwd_ms)},
+        "work": stats,
+        "roofline": {"kernel": "k_build (combinatorial building)", "bound": "alu", "achieved": achieved,
+                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "peak_basis": "FP32: %d SMs x %d lanes x 2 x %.0f MHz" % (props.multi_processor_count,
+                                                                               FP32_LANES, max_mhz),
+                     "algorithmic_flops_per_launch": alg_flops},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": statistics.mean(e2e_ms)},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,210 @@
+/* mkf.h -- C ABI of the GB300 (sm_103a) Kalman-filter track-building library.
+ *
+ * The operations follow the problem statement of the paper (CHEP 2019 mkFit
+ * status report): a lightweight detector of barrel layers at an average radius
+ * and endcap disks at an average z, with a material thickness and a uniform
+ * field (Sec. 2); hits given by their 3-D positions (Sec. 1, Sec. 2); seeds
+ * that start the search (Sec. 1, Sec. 3); combinatorial building that keeps
+ * only the best-ranking candidates up to a per-seed cap (Sec. 2), counts
+ * missing hits and ranks by a score (Sec. 3), keeps short candidates (abstract)
+ * and removes duplicates in a final step (abstract); and the Kalman fit over a
+ * fixed hit assignment (Sec. 1).
+ *
+ * Conventions (every entry point):
+ *  - Array arguments are caller-owned DEVICE pointers unless stated otherwise;
+ *    the library never frees or retains them past the call's stream work.
+ *    Structure of arrays: "[6][S]" means 6 rows of S contiguous floats.
+ *  - Track parameters p = (x, y, z, kappa = q/pT, phi, theta) in cm, 1/GeV,
+ *    rad.  A covariance is the packed lower triangle in row order,
+ *    index(i, j) = i*(i+1)/2 + j for i >= j (21 entries).
+ *  - Work is enqueued asynchronously on `stream` (a cudaStream_t passed as
+ *    void*, NULL = legacy default stream).  Argument errors are reported by
+ *    the return code before anything is enqueued.  Errors detected on the
+ *    device (capacity overflow, bounded waits that expired) are latched in a
+ *    device status word and returned by the next mkf_sync().
+ *  - A context is bound to one device and is not thread safe: use one per
+ *    host thread.  It owns a workspace that grows on demand (cudaMalloc).
+ *  - No C++ exception crosses this interface.
+ */
+#ifndef MKF_H
+#define MKF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int mkf_status;
+#define MKF_OK 0
+#define MKF_ERR_ARG (-1)       /* invalid argument (null pointer, size out of range) */
+#define MKF_ERR_OOM (-2)       /* workspace allocation failed */
+#define MKF_ERR_CUDA (-3)      /* a CUDA runtime call failed */
+#define MKF_ERR_TIMEOUT (-4)   /* a bounded device-side wait expired */
+#define MKF_ERR_STATE (-5)     /* call out of order (e.g. no geometry, hits not binned) */
+#define MKF_ERR_CAPACITY (-6)  /* a device-side fixed-size buffer overflowed; results invalid */
+
+/* Track flags written by mkf_build_tracks / mkf_dedup_tracks. */
+#define MKF_TRK_SHORT 0        /* best candidate has fewer than min_hits hits (or none) */
+#define MKF_TRK_KEPT 1         /* kept after duplicate removal */
+#define MKF_TRK_DUP 2          /* removed as a duplicate of a better-scoring track */
+
+#define MKF_MAX_LAYERS 64
+#define MKF_MAX_CANDS 8
+
+typedef struct mkf_ctx mkf_ctx;
+
+/* Create a context on CUDA device `device`.  *out is set to NULL on failure. */
+mkf_status mkf_create(mkf_ctx** out, int device);
+/* Release the context and its workspace (synchronises the device first). */
+void mkf_destroy(mkf_ctx* ctx);
+/* Text of the last error on this context ("" if none).  Owned by the context. */
+const char* mkf_last_error(const mkf_ctx* ctx);
+/* Wait for all work of the context on `stream`, then read and clear the device
+ * status word: MKF_OK, MKF_ERR_CAPACITY or MKF_ERR_TIMEOUT. */
+mkf_status mkf_sync(mkf_ctx* ctx, void* stream);
+
+/* One detector surface (Sec. 2: barrel layers collapsed at their average
+ * radius, endcap layers at their average z, no modules). */
+typedef struct {
+  int kind;          /* 0: barrel cylinder r = pos; 1: endcap disk z = pos (signed) */
+  float pos;         /* cm */
+  float lo, hi;      /* acceptance: barrel z range, disk r range (cm) */
+  float x_over_x0;   /* material thickness at normal incidence, radiation lengths */
+  int n_phi_bins;    /* hit-lookup bins in phi (0: library default 64) */
+  int n_w_bins;      /* hit-lookup bins in z (barrel) or r (disk) (0: default 16) */
+} mkf_layer;
+
+/* Load the detector description and the uniform field Bz (tesla).  `layers`
+ * is a HOST array of n_layers (1..MKF_MAX_LAYERS) entries; it is copied. */
+mkf_status mkf_load_geometry(mkf_ctx* ctx, const mkf_layer* layers, int n_layers, float bz_tesla);
+
+/* Bin the hits of n_events events for position-based lookup (Sec. 2: the
+ * search relies only on the 3-D hit positions): key = (event, layer, phi bin,
+ * z bin for a barrel / r bin for a disk); counting sort + exclusive scan;
+ * inside one bin hits keep ascending original index.  The binned copy stays in
+ * the context for the following mkf_build_tracks calls.
+ *   xyz [3][H]          global hit positions (cm)
+ *   lcov [3][H]         local covariance (var_rphi, var_b, cov) with b = z on a
+ *                       barrel and r on a disk (cm^2)
+ *   layer [H]           layer index 0..n_layers-1 (out of range: MKF_ERR_ARG at sync)
+ *   ev_hit_off [E+1]    int64 CSR offsets of each event's hits, ev_hit_off[0] = 0,
+ *                       ev_hit_off[E] = H
+ * Hit ids in every output are the caller's indices 0..H-1. */
+mkf_status mkf_bin_hits(mkf_ctx* ctx, const float* xyz, const float* lcov, const int* layer, int64_t n_hits,
+                        const int64_t* ev_hit_off, int n_events, void* stream);
+
+/* Read back the binning (for inspection and tests): perm [H] original id of
+ * each sorted position, bin_off [n_bins_total+1] first sorted position of each
+ * (event, layer, bin), n_bins_total = n_events * sum_l(n_phi_l * n_w_l).
+ * DEVICE output pointers; either may be NULL.  Returns n_bins_total in *n_bins. */
+mkf_status mkf_get_binning(mkf_ctx* ctx, int* perm, int* bin_off, int64_t* n_bins, void* stream);
+
+/* Combinatorial Kalman-filter track building for all seeds of all binned
+ * events (Sec. 1: propagate layer N-1 -> N, update with the hit; Sec. 2: only
+ * the best-ranking candidates are kept per layer, up to max_cands per seed;
+ * Sec. 3: missing hits (holes) counted, candidates ranked by a score;
+ * abstract: short candidates preserved, duplicates removed at the end).
+ * Per step every active candidate moves outward to its next reachable
+ * surface, its covariance is transported and inflated for multiple
+ * scattering, chi2 is evaluated against the hits in a conservative window,
+ * children are formed (one per hit with chi2 < chi2_cut, plus a hole child
+ * while holes <= max_holes), the max_cands best children by
+ * score = 10 n_hits - 10 n_holes - sum chi2 (ties: parent slot, hit id, hole
+ * last) are updated and kept.  A candidate with no next surface or no child
+ * is finished.  The best finished candidate of a seed is its track; tracks
+ * with at least min_hits hits go through greedy duplicate removal per event
+ * (drop a track sharing more than dup_frac of min(n_a, n_b) hits with a
+ * better-scoring kept track).
+ *   seed_par [6][S], seed_cov [21][S]   seed states
+ *   ev_seed_off [E+1]                    int64 CSR offsets of each event's seeds
+ *   max_cands 1..MKF_MAX_CANDS, max_holes >= 0, min_hits >= 0, 0 <= dup_frac <= 1
+ * Outputs ([S] arrays, DEVICE; out_layers, out_counts may be NULL):
+ *   out_hits [S][L]     hit id at the k-th crossed surface, -1 for a hole or past the end
+ *   out_layers [S][L]   surface index of the k-th crossing, -1 past the end
+ *   out_par [6][S], out_cov [21][S]  state of the track at its last surface
+ *   out_score [S], out_chi2 [S]      score and sum of chi2
+ *   out_counts [3][S]   n_hits, n_holes, n_steps
+ *   out_flags [S]       MKF_TRK_* */
+mkf_status mkf_build_tracks(mkf_ctx* ctx, const float* seed_par, const float* seed_cov, const int64_t* ev_seed_off,
+                            int64_t n_seeds, float chi2_cut, int max_cands, int max_holes, int min_hits,
+                            float dup_frac, int* out_hits, int* out_layers, float* out_par, float* out_cov,
+                            float* out_score, float* out_chi2, int* out_counts, int* out_flags, void* stream);
+
+/* Debug switch for mkf_build_tracks: when on, every candidate step also
+ * evaluates chi2 against every hit of the layer and counts accepted hits that
+ * lay outside its search window (statistic 4 of mkf_get_stats; it must be 0). */
+mkf_status mkf_set_debug(mkf_ctx* ctx, int brute_force_window_check);
+
+/* Work counters of the last mkf_build_tracks (synchronises `stream`):
+ * [0] candidate steps, [1] chi2 evaluations, [2] hit updates, [3] tracks kept,
+ * [4] window violations (debug), [5] navigation surface tests, [6] seeds.
+ * HOST output of n <= 8 values. */
+mkf_status mkf_get_stats(mkf_ctx* ctx, int64_t* out, int n, void* stream);
+
+/* Kernel timing.  When on, the library records CUDA events on the launch
+ * stream around its kernels; mkf_get_timings returns the device time of the
+ * most recent call of each stage in milliseconds (synchronises `stream`):
+ * [0] track-building kernel, [1] hit binning (all its kernels), [2] duplicate
+ * removal, [3] forward fit, [4] fit adjoint, [5] backward fit.  A stage not run
+ * since timing was switched on reads as -1.  HOST output of n <= 8 floats. */
+mkf_status mkf_set_timing(mkf_ctx* ctx, int on);
+mkf_status mkf_get_timings(mkf_ctx* ctx, float* ms, int n, void* stream);
+
+/* Duplicate removal alone on given tracks (same rule as in mkf_build_tracks):
+ *   hits [S][L] hit ids (-1 none), score [S], nhits [S], ev_seed_off [E+1]
+ *   out_flags [S]  MKF_TRK_*  */
+mkf_status mkf_dedup_tracks(mkf_ctx* ctx, const int* hits, int L, const float* score, const int* nhits,
+                            const int64_t* ev_seed_off, int n_events, int64_t n_seeds, int64_t n_hits_total,
+                            int min_hits, float dup_frac, int* out_flags, void* stream);
+
+/* Kalman fit over a fixed hit assignment (Sec. 1: "fitting simply applies the
+ * KF procedure to all hits identified during building").  For each listed hit
+ * in crossing order: propagate to that hit's surface, add its material,
+ * update with the hit (no cut).
+ *   xyz [3][H], lcov [3][H], layer [H]   hits (as for mkf_bin_hits)
+ *   hits [T][K]          hit ids in crossing order, -1 entries skipped
+ *   init_par [6][T], init_cov [21][T]
+ *   align [L][3] or NULL  per-layer (dr, dphi, dz): barrel radius and hits
+ *                         shift by dr (radially), hit azimuths by dphi, hit z by
+ *                         dz; for a disk its z and the hits' z shift by dz,
+ *                         hit radii by dr, azimuths by dphi
+ *   x0 [L] or NULL        per-layer thickness overriding the geometry's
+ * Outputs: out_par [6][T], out_cov [21][T], out_chi2 [T] (sum of chi2),
+ *   out_ok [T] or NULL (1: every surface reached),
+ *   ckpt [K][27][T] or NULL: state (6 parameters, 21 covariance) before step k,
+ *   needed by mkf_fit_tracks_adjoint. */
+mkf_status mkf_fit_tracks(mkf_ctx* ctx, const float* xyz, const float* lcov, const int* layer, int64_t n_hits,
+                          const int* hits, int K, const float* init_par, const float* init_cov, int64_t n_tracks,
+                          const float* align, const float* x0, float* out_par, float* out_cov, float* out_chi2,
+                          int* out_ok, float* ckpt, void* stream);
+
+/* Backward (inward) fit: starts from init_par = the forward result at the
+ * outermost listed hit, with the covariance reset to 100 x the seed-style
+ * diagonal (0.01, 0.01, 0.01 cm^2, (0.05 kappa)^2, 0.0025, 0.0025), updates
+ * with the outermost hit in place, then propagates inward (negative path) to
+ * each earlier hit, adds its material and updates.  Arguments as
+ * mkf_fit_tracks (init_cov is ignored; ckpt unsupported, pass NULL). */
+mkf_status mkf_fit_backward(mkf_ctx* ctx, const float* xyz, const float* lcov, const int* layer, int64_t n_hits,
+                            const int* hits, int K, const float* init_par, int64_t n_tracks, const float* align,
+                            const float* x0, float* out_par, float* out_cov, float* out_chi2, int* out_ok,
+                            void* stream);
+
+/* Adjoint (reverse mode) of mkf_fit_tracks.  Not in the paper: gradient of
+ *   loss = sum_t g_chi2[t] chi2_t + g_par[.][t] . p_t + g_cov[.][t] . C_t
+ * (C_t packed) with respect to the hit positions, the per-layer alignment and
+ * the per-layer thickness.  Needs the checkpoints written by the forward call
+ * with the same inputs; recomputes each step's propagation from them.
+ *   g_chi2 [T], g_par [6][T], g_cov [21][T]: upstream gradients, any may be NULL
+ * Outputs (overwritten): g_hit_xyz [3][H], g_align [L][3], g_x0 [L]. */
+mkf_status mkf_fit_tracks_adjoint(mkf_ctx* ctx, const float* xyz, const float* lcov, const int* layer,
+                                  int64_t n_hits, const int* hits, int K, const float* init_par,
+                                  const float* init_cov, int64_t n_tracks, const float* align, const float* x0,
+                                  const float* ckpt, const float* g_chi2, const float* g_par, const float* g_cov,
+                                  float* g_hit_xyz, float* g_align, float* g_x0, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MKF_H */

@@ -10,6 +10,7 @@ type); this module compiles it with g++ on first use and wraps it with ctypes.
 """
 import ctypes
 import os
+import platform
 import subprocess
 import threading
 
@@ -28,11 +29,15 @@ LL = ctypes.POINTER(ctypes.c_longlong)
 
 def build(force=False):
     """Compile the oracle (g++, -O2, no target-specific flags)."""
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+    arch = _LIB + ".arch"
+    arch_ok = os.path.exists(arch) and open(arch).read().strip() == platform.machine()
+    if not force and arch_ok and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
         return _LIB
     tmp = _LIB + ".tmp%d" % os.getpid()
     subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", tmp, _SRC])
     os.replace(tmp, _LIB)
+    with open(arch, "w") as f:
+        f.write(platform.machine())
     return _LIB
 
 

@@ -94,13 +94,16 @@ struct Layer {
 struct Geom {
   std::vector<Layer> layers;
   double bz;
+  double r_max;   // outer radius of the tracking volume
 };
 static Geom make_geom(const double* tab, int L, double bz) {
   Geom g;
   g.bz = bz;
+  g.r_max = 0;
   for (int l = 0; l < L; ++l) {
     const double* t = tab + 5 * l;
     g.layers.push_back(Layer{(int)t[0], t[1], t[2], t[3], t[4]});
+    g.r_max = std::max(g.r_max, (int)t[0] == 0 ? t[1] : t[3]);
   }
   return g;
 }
@@ -381,13 +384,16 @@ struct NavResult {
 static Surf<double> plain_surf(const Layer& ly) { return Surf<double>{ly.kind, ly.pos, ly.lo, ly.hi, ly.x0}; }
 
 // Candidates: barrels with r_L > rho_ref + eps; disks on the side of motion with
-// |z_L| > zeta_ref + eps.  For each, the first crossing s > 0; keep those
+// |z_L| > zeta_ref + eps that are crossed before the particle leaves the
+// tracking volume (r > r_max).  For each, the first crossing s > 0; keep those
 // inside acceptance; the next surface is the one with the smallest s.
 static NavResult next_surface(const Geom& g, const double p[6], double rho_ref, double zeta_ref, Margin* mg) {
   NavResult best;
   std::vector<std::pair<double, int>> acc;
   std::vector<std::pair<double, double>> rejected;   // (s, margin) of crossings outside acceptance
   const double cot = cos(p[5]) / sin(p[5]);
+  bool exit_known = false;
+  double s_exit = 1e300;
   for (int l = 0; l < (int)g.layers.size(); ++l) {
     const Layer& ly = g.layers[l];
     // (a reference equal to a nominal surface position is exact: no margin)
@@ -402,6 +408,17 @@ static NavResult next_surface(const Geom& g, const double p[6], double rho_ref, 
     Surf<double> sf = plain_surf(ly);
     double s;
     if (!surf_path(p, sf, g.bz, +1, s, mg)) continue;
+    if (ly.kind == 1) {
+      // a particle leaving the tracking volume (r > r_max) is lost: the disk
+      // counts only when it is crossed before that exit
+      if (!exit_known) {
+        double se;
+        s_exit = cyl_path(p, g.r_max, g.bz, +1, se, nullptr) ? se : 1e300;
+        exit_known = true;
+      }
+      if (mg) mg->add(fabs(s - s_exit) / std::max(s, 1.0));
+      if (!(s < s_exit)) continue;
+    }
     double q[6];
     helix_at(p, s, g.bz, q);
     double coord = ly.kind == 0 ? q[2] : std::hypot(q[0], q[1]);

@@ -1,0 +1,610 @@
+// build.cu -- combinatorial Kalman-filter track building, persistent kernel.
+//
+// Method (paper Sec. 1-3 and abstract): every candidate of every seed is,
+// step by step, propagated outward to its next reachable surface with its
+// covariance transported and inflated for material; compatible hits are found
+// from the (event, layer, phi, z|r) bins; chi2 is computed for each; children
+// (hits with chi2 < cut, plus a hole child within the hole budget) are ranked
+// by score = 10 n_hits - 10 n_holes - sum chi2 and only the best max_cands per
+// seed are kept (the per-seed cap of Sec. 2); a candidate with no next surface
+// or no child is finished and kept (short candidates, abstract); the best
+// finished candidate is the seed's track.
+//
+// GB300 mapping:
+//  * a seed is owned by a group of N = max_cands consecutive lanes of a warp;
+//    lane k of the group holds candidate slot k (27 floats in registers);
+//  * groups take seeds from a global queue (atomic counter) and refill as soon
+//    as their seed is done, so one launch covers many events of uneven size;
+//  * each lane keeps its own best children (sorted 64-bit keys) while it scans
+//    its window; the group merges them with N rounds of shuffle min-reductions;
+//  * only the selected children are Kalman-updated (the score needs only the
+//    predicted chi2), reading the parent's propagated state from shared memory;
+//  * the parent pointers and hits of every step stay in shared memory and are
+//    walked back once per seed.
+#include "mkf_device.cuh"
+#include "mkf_internal.h"
+
+namespace mkf {
+
+namespace {
+
+constexpr int kWarps = 4;
+constexpr int kThreads = kWarps * 32;
+constexpr int kSlotWords = 32;             // per-lane shared slot: p[6], C[21], score, nh, nholes, rho, zeta
+constexpr uint32_t kHoleKey = 0x0FFFFFFFu;
+constexpr uint32_t kHistHole = 0x3FFFFFu;  // 22-bit local hit index field
+
+// most groups a warp can hold for a given compile-time bound NMAX on max_cands
+// (N is in (NMAX/2, NMAX] for NMAX >= 2)
+template <int NMAX> constexpr int max_groups() { return NMAX == 1 ? 32 : 32 / (NMAX / 2 + 1); }
+
+struct BuildDev {
+  const GeomDev* geom;
+  const float4* rec;
+  const int* bin_off;
+  const float* vmax;
+  const int64_t* ev_hit_off;
+  const float* seed_par;
+  const float* seed_cov;
+  const int64_t* ev_seed_off;
+  int64_t n_seeds;
+  int n_events;
+  float chi2_cut;
+  int ncand;
+  int max_holes;
+  int debug;
+  int* out_hits;
+  int* out_layers;
+  float* out_par;
+  float* out_cov;
+  float* out_score;
+  float* out_chi2;
+  int* out_counts;
+  int* track_nh;
+  unsigned long long* seed_ctr;
+  unsigned long long* stats;
+  int* status;
+};
+
+__device__ __forceinline__ uint32_t ordered(float f) {
+  uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float unordered(uint32_t o) {
+  return __uint_as_float((o & 0x80000000u) ? (o & 0x7FFFFFFFu) : ~o);
+}
+// smaller key = better child: score descending, parent slot, hit id, hole last
+__device__ __forceinline__ uint64_t child_key(float score, int slot, uint32_t hitkey) {
+  return ((uint64_t)(~ordered(score)) << 32) | ((uint64_t)slot << 28) | hitkey;
+}
+
+__device__ __forceinline__ HitRec load_rec(const float4* __restrict__ rec, int pos) {
+  float4 a = __ldg(&rec[2 * pos]);
+  float4 b = __ldg(&rec[2 * pos + 1]);
+  HitRec h;
+  h.c = a.x;
+  h.s = a.y;
+  h.w = a.z;
+  h.v00 = a.w;
+  h.v01 = b.x;
+  h.v11 = b.y;
+  h.orig = __float_as_int(b.z);
+  h.bin = __float_as_int(b.w);
+  return h;
+}
+
+__device__ __forceinline__ int event_of(const int64_t* off, int n_events, int64_t i) {
+  int lo = 0, hi = n_events;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (off[mid] <= i)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// min over the N lanes of a group (cyclic shifts 1, 2, 4 cover N <= 8)
+__device__ __forceinline__ uint64_t group_min(uint64_t v, int gbase, int li, int N) {
+  for (int off = 1; off < N; off <<= 1) {
+    int p = li + off;
+    if (p >= N) p -= N;
+    uint64_t o = __shfl_sync(0xffffffffu, v, gbase + p);
+    v = o < v ? o : v;
+  }
+  return v;
+}
+__device__ __forceinline__ uint64_t group_max(uint64_t v, int gbase, int li, int N) {
+  for (int off = 1; off < N; off <<= 1) {
+    int p = li + off;
+    if (p >= N) p -= N;
+    uint64_t o = __shfl_sync(0xffffffffu, v, gbase + p);
+    v = o > v ? o : v;
+  }
+  return v;
+}
+
+template <int NMAX>
+__global__ void __launch_bounds__(kThreads) k_build(const BuildDev a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  GeomDev& G = *reinterpret_cast<GeomDev*>(smem);
+  {
+    const int4* src = reinterpret_cast<const int4*>(a.geom);
+    int4* dst = reinterpret_cast<int4*>(smem);
+    for (int i = threadIdx.x; i < (int)(sizeof(GeomDev) / 16); i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();
+  const int L = G.n_layers;
+  const int N = a.ncand;
+  const int NG = 32 / N;                      // groups per warp
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int gi = lane / N;
+  const int li = lane - gi * N;
+  const bool gvalid = gi < NG;
+  const int gbase = gi * N;
+  const unsigned gmask = gvalid ? (((1u << N) - 1u) << gbase) : 0u;
+
+  float* slots = reinterpret_cast<float*>(smem + sizeof(GeomDev));                 // [kWarps][32][kSlotWords]
+  constexpr int NGM = max_groups<NMAX>();
+  float* bests = slots + kWarps * 32 * kSlotWords;                                  // [kWarps][NGM][32]
+  uint32_t* hist = reinterpret_cast<uint32_t*>(bests + kWarps * NGM * 32);          // [kWarps][NGM][L][NMAX]
+  float* myslot = slots + (warp * 32 + lane) * kSlotWords;
+  float* gslots = slots + (warp * 32 + gbase) * kSlotWords;
+  float* best = bests + (warp * NGM + (gvalid ? gi : 0)) * 32;
+  uint32_t* ghist = hist + (size_t)(warp * NGM + (gvalid ? gi : 0)) * L * NMAX;
+
+  const float cut = a.chi2_cut;
+  const float ck = G.c_kappa;
+  unsigned long long n_steps = 0, n_chi2 = 0, n_upd = 0, n_nav = 0, n_viol = 0;
+
+  // per-group seed state (replicated over the group's lanes)
+  int64_t seed = -1;
+  int ev = 0, step = 0;
+  int hit_base = 0, ebin = 0;
+  // per-lane candidate
+  bool active = false;
+  float p[6], C[21];
+  float score = 0.f, rho = 0.f, zeta = 0.f;
+  int nh = 0, nholes = 0;
+
+  // Take the next seed for every group with want == true.  Called by all lanes
+  // of the warp together (it shuffles).
+  auto fetch = [&](bool want) {
+    unsigned long long s = 0;
+    if (want && gvalid && li == 0) s = atomicAdd(a.seed_ctr, 1ull);
+    s = __shfl_sync(0xffffffffu, s, gbase);
+    if (!want) return;
+    seed = (gvalid && (int64_t)s < a.n_seeds) ? (int64_t)s : -1;
+    active = false;
+    step = 0;
+    if (seed >= 0) {
+      ev = event_of(a.ev_seed_off, a.n_events, seed);
+      hit_base = (int)a.ev_hit_off[ev];
+      ebin = ev * G.bins_per_event;
+      if (li == 0) {
+        active = true;
+        const int64_t S = a.n_seeds;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) p[k] = a.seed_par[k * S + seed];
+#pragma unroll
+        for (int k = 0; k < 21; ++k) C[k] = a.seed_cov[k * S + seed];
+        score = 0.f;
+        nh = nholes = 0;
+        rho = sqrtf(fmaf(p[0], p[0], p[1] * p[1]));
+        zeta = fabsf(p[2]);
+        best[30] = __int_as_float(-2);   // no finished candidate yet
+        atomicAdd(&a.stats[6], 1ull);
+      }
+    }
+  };
+  fetch(gvalid);
+
+  for (;;) {
+    if (__all_sync(0xffffffffu, seed < 0)) break;
+    // ---- (0) save the pre-step state: finished candidates are read back from here
+    if (active) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) myslot[k] = p[k];
+#pragma unroll
+      for (int k = 0; k < 21; ++k) myslot[6 + k] = C[k];
+      myslot[27] = score;
+      myslot[28] = __int_as_float(nh);
+      myslot[29] = __int_as_float(nholes);
+      myslot[30] = rho;
+      myslot[31] = zeta;
+    }
+    // ---- (1) navigation: next reachable surface outward
+    int nl = -1;
+    float ns = INFINITY;
+    float sin_t = 1.f, cos_t = 0.f, cot_t = 0.f, omega = 0.f;
+    if (active && step < L) {
+      sincosf(p[5], &sin_t, &cos_t);
+      cot_t = cos_t / sin_t;
+      omega = ck * p[3];
+      float sph, cph;
+      sincosf(p[4], &sph, &cph);
+      for (int i = 0; i < G.n_barrel; ++i) {
+        const int l = G.barrel_order[i];
+        const LayerDev& ly = G.L[l];
+        if (!(ly.pos > rho + kNavEps)) continue;
+        ++n_nav;
+        const float s = cylinder_path(p[0], p[1], cph, sph, omega, ly.pos, +1);
+        if (!(s < INFINITY)) break;    // the particle's circle stays inside: larger radii too
+        const float z = fmaf(s, cot_t, p[2]);
+        if (z >= ly.lo && z <= ly.hi) {
+          nl = l;
+          ns = s;
+          break;
+        }
+      }
+      if (cot_t != 0.0f) {
+        const int nd = cot_t > 0.f ? G.n_dpos : G.n_dneg;
+        const int8_t* ord = cot_t > 0.f ? G.dpos_order : G.dneg_order;
+        // a particle leaving the tracking volume is lost: disks count only
+        // when crossed before r = r_max
+        float s_lim = ns;
+        bool exit_known = false;
+        for (int i = 0; i < nd; ++i) {
+          const int l = ord[i];
+          const LayerDev& ly = G.L[l];
+          if (!(fabsf(ly.pos) > zeta + kNavEps)) continue;
+          if (!exit_known) {
+            s_lim = fminf(ns, cylinder_path(p[0], p[1], cph, sph, omega, G.r_max, +1));
+            exit_known = true;
+          }
+          ++n_nav;
+          const float s = plane_path(p[2], cot_t, ly.pos, +1);
+          if (!(s < s_lim)) break;     // |z| ordered: later disks are farther
+          const auto h = helix_at(p[0], p[1], p[2], p[4], cot_t, omega, s);
+          const float r = sqrtf(fmaf(h.x, h.x, h.y * h.y));
+          if (r >= ly.lo && r <= ly.hi) {
+            nl = l;
+            ns = s;
+            break;
+          }
+        }
+      }
+    }
+    // ---- (2) propagate, transport the covariance, material; (3) window scan
+    uint64_t keys[NMAX];
+    int kpos[NMAX];
+#pragma unroll
+    for (int k = 0; k < NMAX; ++k) {
+      keys[k] = ~0ull;
+      kpos[k] = -1;
+    }
+    int nk = 0;
+    int kind = 0;
+    if (nl >= 0) {
+      ++n_steps;
+      const LayerDev ly = G.L[nl];
+      kind = ly.kind;
+      const auto h = helix_at(p[0], p[1], p[2], p[4], cot_t, omega, ns);
+      const auto J = transport_jacobian(kind, p, h, ns, omega, ck, cot_t, sin_t);
+      similarity(J, C);
+      p[0] = h.x;
+      p[1] = h.y;
+      p[2] = h.z;
+      p[4] = wrap_phi(h.phi);
+      add_material(kind, ly.x0, h.x, h.y, h.cphi, h.sphi, p[3], sin_t, cos_t, C);
+      const float rc = sqrtf(fmaf(h.x, h.x, h.y * h.y));
+      const float nrho = kind == 0 ? ly.pos : fmaxf(rho, rc);
+      const float nzeta = kind == 0 ? fmaxf(zeta, fabsf(h.z)) : fabsf(ly.pos);
+      // conservative window: |r_i| < sqrt(cut R_ii) (Cauchy-Schwarz), R_ii bounded
+      // by the largest eigenvalue of C_xy (or C_zz) plus the layer's largest hit variance
+      const float va = __ldg(&a.vmax[2 * (ev * L + nl)]);
+      const float vb = __ldg(&a.vmax[2 * (ev * L + nl) + 1]);
+      const float cxx = C[ci(0, 0)], cyy = C[ci(1, 1)], cxy = C[ci(1, 0)];
+      const float hd = 0.5f * (cxx - cyy);
+      const float lam = 0.5f * (cxx + cyy) + sqrtf(fmaf(hd, hd, cxy * cxy));
+      const float ha = sqrtf(cut * (lam + va)) * 1.05f + 1e-4f;
+      const float hb = sqrtf(cut * ((kind == 0 ? C[ci(2, 2)] : lam) + vb)) * 1.05f + 1e-4f;
+      const float phic = atan2f(h.y, h.x);
+      float dphi = ha >= rc ? 0.5f * kPi : asinf(ha / rc);
+      dphi = dphi * 1.001f + 1e-5f;
+      int b0, nb;
+      {
+        const float lo_f = floorf((phic - dphi + kPi) * ly.phi_scale);
+        const float hi_f = floorf((phic + dphi + kPi) * ly.phi_scale);
+        b0 = (int)lo_f;
+        nb = min((int)(hi_f - lo_f) + 1, ly.nphi);
+      }
+      float wlo, whi;
+      if (kind == 0) {
+        wlo = h.z - hb;
+        whi = h.z + hb;
+      } else {
+        wlo = fmaf(rc, cosf(fminf(dphi, 0.5f * kPi)), -hb);
+        whi = rc + hb;
+      }
+      const int iw0 = min(max((int)floorf((wlo - ly.lo) * ly.w_scale), 0), ly.nw - 1);
+      const int iw1 = min(max((int)floorf((whi - ly.lo) * ly.w_scale), 0), ly.nw - 1);
+      const int base = ebin + ly.bin_base;
+      for (int k = 0; k < nb; ++k) {
+        int b = (b0 + k) % ly.nphi;
+        if (b < 0) b += ly.nphi;
+        const int beg = __ldg(&a.bin_off[base + b * ly.nw + iw0]);
+        const int end = __ldg(&a.bin_off[base + b * ly.nw + iw1 + 1]);
+        for (int q = beg; q < end; ++q) {
+          const HitRec hr = load_rec(a.rec, q);
+          const float chi2 = hit_chi2(kind, p, C, hr);
+          ++n_chi2;
+          if (chi2 < cut) {
+            uint64_t kk = child_key(score + 10.0f - chi2, li, (uint32_t)hr.orig);
+            int kp = q;
+#pragma unroll
+            for (int j = 0; j < NMAX; ++j) {
+              if (kk < keys[j]) {
+                uint64_t tk = keys[j];
+                keys[j] = kk;
+                kk = tk;
+                int tp = kpos[j];
+                kpos[j] = kp;
+                kp = tp;
+              }
+            }
+            ++nk;
+          }
+        }
+      }
+      if (a.debug) {
+        // brute force over the whole layer: accepted hits must lie in the window
+        const int beg = __ldg(&a.bin_off[base]);
+        const int end = __ldg(&a.bin_off[base + ly.nphi * ly.nw]);
+        for (int q = beg; q < end; ++q) {
+          const HitRec hr = load_rec(a.rec, q);
+          if (hit_chi2(kind, p, C, hr) < cut) {
+            const int lb = hr.bin - ly.bin_base;
+            const int ip = lb / ly.nw, iw = lb - ip * ly.nw;
+            int d = (ip - b0) % ly.nphi;
+            if (d < 0) d += ly.nphi;
+            if (!(iw >= iw0 && iw <= iw1 && d < nb)) ++n_viol;
+          }
+        }
+      }
+      if (nholes + 1 <= a.max_holes) {
+        uint64_t kk = child_key(score - 10.0f, li, kHoleKey);
+        int kp = -1;
+#pragma unroll
+        for (int j = 0; j < NMAX; ++j) {
+          if (kk < keys[j]) {
+            uint64_t tk = keys[j];
+            keys[j] = kk;
+            kk = tk;
+            int tp = kpos[j];
+            kpos[j] = kp;
+            kp = tp;
+          }
+        }
+        ++nk;
+      }
+      if (nk > 0) {
+        // publish the propagated state for the children to clone
+#pragma unroll
+        for (int k = 0; k < 6; ++k) myslot[k] = p[k];
+#pragma unroll
+        for (int k = 0; k < 21; ++k) myslot[6 + k] = C[k];
+        myslot[30] = nrho;
+        myslot[31] = nzeta;
+        myslot[29] = __int_as_float(nholes | (nl << 16));
+      }
+    }
+    const bool finishing = active && (nl < 0 || nk == 0);
+    __syncwarp();
+    // ---- (4) per-seed selection: N rounds of group min over the lanes' heads
+    uint64_t my_child = ~0ull;
+    int my_pos = -1;
+    for (int r = 0; r < N; ++r) {
+      const uint64_t head = keys[0];
+      const uint64_t bestk = group_min(head, gbase, li, N);
+      const bool win = (head == bestk) && bestk != ~0ull && gvalid;
+      const unsigned wm = __ballot_sync(0xffffffffu, win) & gmask;
+      const int wl = wm ? __ffs(wm) - 1 : lane;
+      const int wpos = __shfl_sync(0xffffffffu, kpos[0], wl);
+      if (li == r && wm) {
+        my_child = bestk;
+        my_pos = wpos;
+      }
+      if (win) {
+#pragma unroll
+        for (int j = 0; j < NMAX - 1; ++j) {
+          keys[j] = keys[j + 1];
+          kpos[j] = kpos[j + 1];
+        }
+        keys[NMAX - 1] = ~0ull;
+        kpos[NMAX - 1] = -1;
+      }
+    }
+    // ---- (5) finished candidates: keep the group's best (score, then earlier step, lower slot)
+    {
+      const uint64_t fk = finishing ? (((uint64_t)ordered(score) << 32) | (uint32_t)(NMAX - li)) : 0ull;
+      const uint64_t fb = group_max(fk, gbase, li, N);
+      if (finishing && fk == fb) {
+        const int last = __float_as_int(best[30]);
+        if (last == -2 || score > best[27]) {
+#pragma unroll
+          for (int k = 0; k < 27; ++k) best[k] = myslot[k];
+          best[27] = score;
+          best[28] = __int_as_float(nh);
+          best[29] = __int_as_float(nholes);
+          best[30] = __int_as_float(step - 1);
+          best[31] = __int_as_float(li);
+        }
+      }
+    }
+    __syncwarp();
+    // ---- (6) Kalman update of the selected children
+    active = false;
+    if (my_child != ~0ull) {
+      const int parent = (int)((my_child >> 28) & 0xFu);
+      const uint32_t hk = (uint32_t)(my_child & 0x0FFFFFFFu);
+      const float* ps = gslots + parent * kSlotWords;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) p[k] = ps[k];
+#pragma unroll
+      for (int k = 0; k < 21; ++k) C[k] = ps[6 + k];
+      nh = __float_as_int(ps[28]);
+      const int packed = __float_as_int(ps[29]);
+      nholes = packed & 0xFFFF;
+      const int lay = packed >> 16;
+      rho = ps[30];
+      zeta = ps[31];
+      score = unordered(~(uint32_t)(my_child >> 32));
+      uint32_t hloc = kHistHole;
+      if (hk != kHoleKey) {
+        const HitRec hr = load_rec(a.rec, my_pos);
+        kf_update(G.L[lay].kind, p, C, hr);
+        ++nh;
+        ++n_upd;
+        hloc = (uint32_t)(my_pos - hit_base);
+        if (hloc >= kHistHole) atomicOr(a.status, kStatCapacity);
+      } else {
+        ++nholes;
+      }
+      ghist[step * NMAX + li] = (hloc & kHistHole) | ((uint32_t)lay << 22) | ((uint32_t)parent << 28);
+      active = true;
+    }
+    __syncwarp();
+    // ---- (7) seed done: write the track, take the next seed
+    const bool any = (__ballot_sync(0xffffffffu, active) & gmask) != 0;
+    const bool done = seed >= 0 && !any;
+    if (done) {
+      const int64_t S = a.n_seeds;
+      const int last = __float_as_int(best[30]);
+      const int bslot = __float_as_int(best[31]);
+      for (int k = li; k < 27; k += N) {
+        if (k < 6)
+          a.out_par[k * S + seed] = best[k];
+        else
+          a.out_cov[(k - 6) * S + seed] = best[k];
+      }
+      if (li == 0) {
+        const int bnh = __float_as_int(best[28]);
+        const int bho = __float_as_int(best[29]);
+        const float bsc = best[27];
+        a.out_score[seed] = bsc;
+        a.out_chi2[seed] = 10.0f * (float)(bnh - bho) - bsc;
+        a.track_nh[seed] = bnh;
+        if (a.out_counts) {
+          a.out_counts[seed] = bnh;
+          a.out_counts[S + seed] = bho;
+          a.out_counts[2 * S + seed] = last + 1;
+        }
+        int* oh = a.out_hits + seed * L;
+        int* ol = a.out_layers ? a.out_layers + seed * L : nullptr;
+        for (int k = last + 1; k < L; ++k) {
+          oh[k] = -1;
+          if (ol) ol[k] = -1;
+        }
+        int slot = bslot;
+        for (int k = last; k >= 0; --k) {
+          const uint32_t e = ghist[k * NMAX + slot];
+          const uint32_t hl = e & kHistHole;
+          oh[k] = hl == kHistHole ? -1 : load_rec(a.rec, hit_base + (int)hl).orig;
+          if (ol) ol[k] = (int)((e >> 22) & 0x3Fu);
+          slot = (int)(e >> 28);
+        }
+      }
+    } else if (seed >= 0) {
+      ++step;
+    }
+    __syncwarp();
+    fetch(done);
+    __syncwarp();
+  }
+  // ---- counters
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    n_steps += __shfl_xor_sync(0xffffffffu, n_steps, o);
+    n_chi2 += __shfl_xor_sync(0xffffffffu, n_chi2, o);
+    n_upd += __shfl_xor_sync(0xffffffffu, n_upd, o);
+    n_nav += __shfl_xor_sync(0xffffffffu, n_nav, o);
+    n_viol += __shfl_xor_sync(0xffffffffu, n_viol, o);
+  }
+  if (lane == 0) {
+    atomicAdd(&a.stats[0], n_steps);
+    atomicAdd(&a.stats[1], n_chi2);
+    atomicAdd(&a.stats[2], n_upd);
+    atomicAdd(&a.stats[4], n_viol);
+    atomicAdd(&a.stats[5], n_nav);
+  }
+}
+
+template <int NMAX>
+size_t build_smem(int L) {
+  return sizeof(GeomDev) + (size_t)kWarps * 32 * kSlotWords * 4 + (size_t)kWarps * max_groups<NMAX>() * 32 * 4 +
+         (size_t)kWarps * max_groups<NMAX>() * L * NMAX * 4;
+}
+
+template <int NMAX>
+cudaError_t run_build(mkf_ctx* ctx, const BuildDev& d, cudaStream_t st) {
+  const size_t sm = build_smem<NMAX>(ctx->geom.n_layers);
+  cudaError_t e = cudaFuncSetAttribute(k_build<NMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build<NMAX>, kThreads, sm);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  int64_t groups_needed = (d.n_seeds + (32 / d.ncand) - 1) / (32 / d.ncand);
+  int64_t blocks = (groups_needed + kWarps - 1) / kWarps;
+  int64_t grid = (int64_t)ctx->n_sm * per_sm;
+  if (blocks < grid) grid = blocks;
+  if (grid < 1) grid = 1;
+  ctx->tick(kTBuild, st);
+  k_build<NMAX><<<(unsigned)grid, kThreads, sm, st>>>(d);
+  ctx->tock(kTBuild, st);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_build(mkf_ctx* ctx, const BuildArgs& a, cudaStream_t st) {
+  cudaError_t e;
+  const int64_t S = a.n_seeds;
+  if ((e = ctx->track_hits.ensure((size_t)(S > 0 ? S : 1) * 4)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(ctx->seed_ctr.p, 0, sizeof(unsigned long long), st))) return e;
+  if ((e = cudaMemsetAsync(ctx->stats.p, 0, 8 * sizeof(int64_t), st))) return e;
+  if (S > 0) {
+    BuildDev d;
+    d.geom = ctx->geom_dev.as<GeomDev>();
+    d.rec = ctx->rec.as<float4>();
+    d.bin_off = ctx->bin_off.as<int>();
+    d.vmax = ctx->vmax.as<float>();
+    d.ev_hit_off = ctx->ev_hit_off.as<int64_t>();
+    d.seed_par = a.seed_par;
+    d.seed_cov = a.seed_cov;
+    d.ev_seed_off = a.ev_seed_off;
+    d.n_seeds = S;
+    d.n_events = ctx->n_events;
+    d.chi2_cut = a.chi2_cut;
+    d.ncand = a.max_cands;
+    d.max_holes = a.max_holes;
+    d.debug = ctx->debug_window;
+    d.out_hits = a.out_hits;
+    d.out_layers = a.out_layers;
+    d.out_par = a.out_par;
+    d.out_cov = a.out_cov;
+    d.out_score = a.out_score;
+    d.out_chi2 = a.out_chi2;
+    d.out_counts = a.out_counts;
+    d.track_nh = ctx->track_hits.as<int>();
+    d.seed_ctr = ctx->seed_ctr.as<unsigned long long>();
+    d.stats = ctx->stats.as<unsigned long long>();
+    d.status = ctx->status.as<int>();
+    if (a.max_cands <= 1)
+      e = run_build<1>(ctx, d, st);
+    else if (a.max_cands <= 2)
+      e = run_build<2>(ctx, d, st);
+    else if (a.max_cands <= 4)
+      e = run_build<4>(ctx, d, st);
+    else
+      e = run_build<8>(ctx, d, st);
+    if (e != cudaSuccess) return e;
+  }
+  return launch_dedup(ctx, a.out_hits, ctx->geom.n_layers, a.out_score, ctx->track_hits.as<int>(), a.ev_seed_off,
+                      ctx->n_events, S, ctx->n_hits, a.min_hits, a.dup_frac, a.out_flags, st);
+}
+
+}  // namespace mkf

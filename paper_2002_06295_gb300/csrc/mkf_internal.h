@@ -1,0 +1,149 @@
+// mkf_internal.h -- context, device geometry table and launch declarations
+// shared by the translation units of the library (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "mkf.h"
+
+namespace mkf {
+
+// Device status bits (latched, read and cleared by mkf_sync).
+enum : int {
+  kStatCapacity = 1,   // a fixed-size device buffer overflowed
+  kStatTimeout = 2,    // a bounded wait / iteration limit expired
+  kStatBadInput = 4,   // an input index was out of range (skipped)
+};
+
+struct LayerDev {
+  int kind;
+  float pos, lo, hi, x0;
+  int nphi, nw, bin_base;
+  float phi_scale;   // nphi / (2 pi)
+  float w_scale;     // nw / (hi - lo)
+  float pad0, pad1;
+};
+
+struct GeomDev {
+  int n_layers;
+  float bz;
+  float c_kappa;         // -alpha * bz: omega = c_kappa * kappa
+  int bins_per_event;
+  int n_barrel, n_dpos, n_dneg;
+  float r_max;           // outer radius of the tracking volume
+  int8_t barrel_order[MKF_MAX_LAYERS];   // barrel ids by increasing r
+  int8_t dpos_order[MKF_MAX_LAYERS];     // z > 0 disk ids by increasing z
+  int8_t dneg_order[MKF_MAX_LAYERS];     // z < 0 disk ids by increasing |z|
+  LayerDev L[MKF_MAX_LAYERS];
+};
+
+// Grow-only device buffer owned by the context.
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  cudaError_t ensure(size_t bytes) {
+    if (bytes <= cap) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    size_t want = bytes < 256 ? 256 : bytes;
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e == cudaSuccess) cap = want;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+  template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+struct BuildArgs {
+  const float* seed_par;
+  const float* seed_cov;
+  const int64_t* ev_seed_off;
+  int64_t n_seeds;
+  float chi2_cut;
+  int max_cands, max_holes, min_hits;
+  float dup_frac;
+  int* out_hits;
+  int* out_layers;
+  float* out_par;
+  float* out_cov;
+  float* out_score;
+  float* out_chi2;
+  int* out_counts;
+  int* out_flags;
+};
+
+}  // namespace mkf
+
+namespace mkf {
+enum TimerId { kTBuild = 0, kTBin = 1, kTDedup = 2, kTFit = 3, kTAdjoint = 4, kTBackward = 5, kTimers = 8 };
+}
+
+struct mkf_ctx {
+  int device = 0;
+  int n_sm = 0;
+  std::string err;
+  bool have_geom = false;
+  mkf::GeomDev geom{};
+  mkf::DevBuf geom_dev;
+  int debug_window = 0;
+
+  // binning
+  bool binned = false;
+  int64_t n_hits = 0;
+  int n_events = 0;
+  int64_t n_bins_total = 0;
+  mkf::DevBuf rec, perm, bin_off, bin_cnt, keys, ranks, vmax, ev_hit_off, scan_part;
+
+  // build / dedup
+  mkf::DevBuf seed_ctr, stats, status, dd_head, dd_next, dd_beat, dd_nbeat, dd_state, track_hits;
+
+  // optional stage timing (CUDA events on the launch stream)
+  int timing = 0;
+  bool timers_made = false;
+  bool timer_used[mkf::kTimers] = {};
+  cudaEvent_t t_beg[mkf::kTimers] = {}, t_end[mkf::kTimers] = {};
+  void tick(int i, cudaStream_t st) {
+    if (timing && timers_made) cudaEventRecord(t_beg[i], st);
+  }
+  void tock(int i, cudaStream_t st) {
+    if (timing && timers_made) {
+      cudaEventRecord(t_end[i], st);
+      timer_used[i] = true;
+    }
+  }
+
+  mkf_status fail(mkf_status code, const std::string& msg) {
+    err = msg;
+    return code;
+  }
+  mkf_status cuda_fail(cudaError_t e, const char* what) {
+    err = std::string(what) + ": " + cudaGetErrorString(e);
+    return MKF_ERR_CUDA;
+  }
+};
+
+namespace mkf {
+// launchers (each returns the first CUDA error, or cudaSuccess)
+cudaError_t launch_bin_hits(mkf_ctx* ctx, const float* xyz, const float* lcov, const int* layer, int64_t n_hits,
+                            const int64_t* ev_hit_off, int n_events, cudaStream_t st);
+cudaError_t launch_build(mkf_ctx* ctx, const BuildArgs& a, cudaStream_t st);
+cudaError_t launch_dedup(mkf_ctx* ctx, const int* hits, int L, const float* score, const int* nhits,
+                         const int64_t* ev_seed_off, int n_events, int64_t n_seeds, int64_t n_hits_total,
+                         int min_hits, float dup_frac, int* out_flags, cudaStream_t st);
+cudaError_t launch_fit(mkf_ctx* ctx, int direction, const float* xyz, const float* lcov, const int* layer,
+                       int64_t n_hits, const int* hits, int K, const float* init_par, const float* init_cov,
+                       int64_t n_tracks, const float* align, const float* x0, float* out_par, float* out_cov,
+                       float* out_chi2, int* out_ok, float* ckpt, cudaStream_t st);
+cudaError_t launch_fit_adjoint(mkf_ctx* ctx, const float* xyz, const float* lcov, const int* layer, int64_t n_hits,
+                               const int* hits, int K, const float* init_par, const float* init_cov,
+                               int64_t n_tracks, const float* align, const float* x0, const float* ckpt,
+                               const float* g_chi2, const float* g_par, const float* g_cov, float* g_hit,
+                               float* g_align, float* g_x0, cudaStream_t st);
+}  // namespace mkf

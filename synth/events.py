@@ -112,6 +112,12 @@ def _cylinder_path(x, y, phi, omega, r):
     return best
 
 
+def tracking_radius(geom):
+    """Outer radius of the tracking volume: the largest barrel radius or disk
+    outer edge."""
+    return float(max(np.max(np.where(geom.kind == KIND_BARREL, geom.pos, geom.hi)), 0.0))
+
+
 def _highland(t_eff, kappa, theta):
     p = 1.0 / (np.abs(kappa) * np.sin(theta))
     beta_p = p * p / np.sqrt(p * p + PION_MASS ** 2)
@@ -123,6 +129,7 @@ def simulate_event(geom: Geometry, n_tracks: int, rng: np.random.Generator, *,
                    seed_smear=0.05, kick=True):
     L = geom.n_layers
     T = n_tracks
+    r_max = tracking_radius(geom)
     if pt_log:
         pt = np.exp(rng.uniform(np.log(pt_range[0]), np.log(pt_range[1]), T))
     else:
@@ -152,6 +159,7 @@ def simulate_event(geom: Geometry, n_tracks: int, rng: np.random.Generator, *,
         idx = np.nonzero(alive)[0]
         xs, ys, zs, ps, ts, om = x[idx], y[idx], z[idx], phi[idx], theta[idx], omega[idx]
         cot = np.cos(ts) / np.sin(ts)
+        s_exit = _cylinder_path(xs, ys, ps, om, r_max)
         S = np.full((idx.size, L), np.inf)
         for l in range(L):
             if geom.kind[l] == KIND_BARREL:
@@ -167,6 +175,9 @@ def simulate_event(geom: Geometry, n_tracks: int, rng: np.random.Generator, *,
                 with np.errstate(divide="ignore", invalid="ignore"):
                     s = np.where(cand, (zl - zs) / cot, np.inf)
                 s = np.where(s > 0, s, np.inf)
+                # a particle that leaves the tracking volume (r > r_max) is lost:
+                # the disk must be crossed before the exit
+                s = np.where(s < s_exit, s, np.inf)
                 fin = np.isfinite(s)
                 sx = np.where(fin, s, 0.0)
                 px, py, _ = _position_at(xs, ys, zs, ps, cot, om, sx)

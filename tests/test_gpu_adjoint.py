@@ -1,0 +1,149 @@
+"""The hand-written adjoint of the Kalman fit (through the C ABI and through
+torch.autograd) against the oracle's dual-number gradient and FP64 central
+finite differences (h = 1e-6): within 1e-3 relative."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from _util import f32, i32, make_ctx
+
+pytestmark = pytest.mark.gpu
+
+GRAD_RTOL = 1e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _inputs(n=300, seed=21, geom=None, pt=(1.0, 10.0), eta=0.8):
+    g = geom or synth.geometry_barrel14()
+    rng = np.random.default_rng(seed)
+    ev = synth.simulate_event(g, n, rng, pt_range=pt, eta_max=eta)
+    keep = (ev.true_hits >= 0).sum(1) >= min(g.n_layers, 6)
+    hits, sp, sc = ev.true_hits[keep], ev.seed_par[keep], ev.seed_cov[keep]
+    # inputs quantised to float32 so that both sides see the same numbers
+    q = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    ev.hit_xyz, ev.hit_lcov = q(ev.hit_xyz), q(ev.hit_lcov)
+    align = q(rng.normal(0, 1e-3, (g.n_layers, 3)))
+    x0 = q(g.x0 * (1 + 0.2 * rng.random(g.n_layers)))
+    T = hits.shape[0]
+    up = dict(g_chi2=q(rng.normal(size=T)), g_par=q(rng.normal(size=(T, 6)) * [1, 1, 1, 10, 1, 1]),
+              g_cov=q(rng.normal(size=(T, 21)) * 100))
+    return g, ev, hits, q(sp), q(sc), align, x0, up
+
+
+def _group_errors(got, ref):
+    err = np.abs(got - ref)
+    scale = np.maximum(np.abs(ref), 0.01 * np.abs(ref).max())
+    return float(np.max(err / scale)), float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+
+
+@pytest.mark.parametrize("upstream", ["chi2", "all"])
+def test_adjoint_matches_oracle_gradient(upstream):
+    import oracle
+    import paper_2002_06295_gb300 as mkf
+    g, ev, hits, sp, sc, align, x0, up = _inputs()
+    if upstream == "chi2":
+        up = dict(g_chi2=up["g_chi2"], g_par=None, g_cov=None)
+    dev = torch.device("cuda", 0)
+    ctx = make_ctx(g)
+    T, K = hits.shape
+    xyz_d, lcov_d, lay_d, hits_d = f32(ev.hit_xyz.T, dev), f32(ev.hit_lcov.T, dev), i32(ev.hit_layer, dev), i32(hits, dev)
+    sp_d, sc_d, al_d, x0_d = f32(sp.T, dev), f32(sc.T, dev), f32(align, dev), f32(x0, dev)
+    ckpt = torch.empty((K, 27, T), dtype=torch.float32, device=dev)
+    mkf.mkf_fit_tracks(ctx, xyz_d, lcov_d, lay_d, hits_d, sp_d, sc_d, align=al_d, x0=x0_d, ckpt=ckpt)
+    gd = {k: (None if v is None else f32(v.T if v.ndim == 2 else v, dev)) for k, v in up.items()}
+    out = mkf.mkf_fit_tracks_adjoint(ctx, xyz_d, lcov_d, lay_d, hits_d, sp_d, sc_d, ckpt, align=al_d, x0=x0_d, **gd)
+    mkf.mkf_sync(ctx)
+    gh = out["g_hit"].cpu().numpy().T.astype(np.float64)
+    ga = out["g_align"].cpu().numpy().astype(np.float64)
+    gx = out["g_x0"].cpu().numpy().astype(np.float64)
+    rh, ra, rx = oracle.fit_grad(oracle.Geo.of(g), ev.hit_xyz, ev.hit_lcov, ev.hit_layer, hits, sp, sc, up["g_chi2"],
+                                 g_par=up["g_par"], g_cov=up["g_cov"], align=align, x0=x0)
+    used = np.unique(hits[hits >= 0])
+    report = {}
+    for name, a, b in (("hit_x", gh[used, 0], rh[used, 0]), ("hit_y", gh[used, 1], rh[used, 1]),
+                       ("hit_z", gh[used, 2], rh[used, 2]), ("align_dr", ga[:, 0], ra[:, 0]),
+                       ("align_dphi", ga[:, 1], ra[:, 1]), ("align_dz", ga[:, 2], ra[:, 2]), ("x0", gx, rx)):
+        report[name] = _group_errors(a, b)
+    print("adjoint vs oracle (max elementwise, norm-wise):", report)
+    for name, (emax, enorm) in report.items():
+        assert enorm < GRAD_RTOL, (name, report)
+        assert emax < 10 * GRAD_RTOL, (name, report)
+    ctx.close()
+
+
+def test_adjoint_matches_central_differences():
+    """FP64 central differences of the oracle's fit, h = 1e-6, on a few inputs."""
+    import oracle
+    import paper_2002_06295_gb300 as mkf
+    g, ev, hits, sp, sc, align, x0, up = _inputs(n=40, seed=22)
+    dev = torch.device("cuda", 0)
+    ctx = make_ctx(g)
+    T, K = hits.shape
+    geo = oracle.Geo.of(g)
+    xyz_d, lcov_d, lay_d, hits_d = f32(ev.hit_xyz.T, dev), f32(ev.hit_lcov.T, dev), i32(ev.hit_layer, dev), i32(hits, dev)
+    sp_d, sc_d, al_d, x0_d = f32(sp.T, dev), f32(sc.T, dev), f32(align, dev), f32(x0, dev)
+    ckpt = torch.empty((K, 27, T), dtype=torch.float32, device=dev)
+    mkf.mkf_fit_tracks(ctx, xyz_d, lcov_d, lay_d, hits_d, sp_d, sc_d, align=al_d, x0=x0_d, ckpt=ckpt)
+    out = mkf.mkf_fit_tracks_adjoint(ctx, xyz_d, lcov_d, lay_d, hits_d, sp_d, sc_d, ckpt, align=al_d, x0=x0_d,
+                                     g_chi2=f32(up["g_chi2"], dev))
+    mkf.mkf_sync(ctx)
+    gh = out["g_hit"].cpu().numpy().T
+    ga = out["g_align"].cpu().numpy()
+    gx = out["g_x0"].cpu().numpy()
+
+    def loss(hx=ev.hit_xyz, al=align, xx=x0):
+        _, _, chi2, _ = oracle.fit(geo, hx, ev.hit_lcov, ev.hit_layer, hits, sp, sc, align=al, x0=xx)
+        return float(up["g_chi2"] @ chi2)
+
+    h = 1e-6
+    rng = np.random.default_rng(5)
+    for hid in rng.choice(np.unique(hits[hits >= 0]), 8, replace=False):
+        for c in range(3):
+            a = ev.hit_xyz.copy(); b = a.copy(); a[hid, c] += h; b[hid, c] -= h
+            fd = (loss(hx=a) - loss(hx=b)) / (2 * h)
+            assert abs(gh[hid, c] - fd) <= GRAD_RTOL * max(abs(fd), 1e-2 * np.abs(gh).max()), (hid, c, gh[hid, c], fd)
+    for l in (0, 6, 13):
+        for c in range(3):
+            a = align.copy(); b = align.copy(); a[l, c] += h; b[l, c] -= h
+            fd = (loss(al=a) - loss(al=b)) / (2 * h)
+            assert abs(ga[l, c] - fd) <= GRAD_RTOL * max(abs(fd), 1e-2 * np.abs(ga[:, c]).max()), (l, c, ga[l, c], fd)
+        a = x0.copy(); b = x0.copy(); a[l] += h; b[l] -= h
+        fd = (loss(xx=a) - loss(xx=b)) / (2 * h)
+        assert abs(gx[l] - fd) <= GRAD_RTOL * max(abs(fd), 1e-2 * np.abs(gx).max()), (l, gx[l], fd)
+    ctx.close()
+
+
+def test_autograd_function():
+    """torch.autograd through the C ABI: the gradient of a scalar loss equals
+    the direct adjoint call; inputs without requires_grad get no gradient."""
+    import paper_2002_06295_gb300 as mkf
+    from paper_2002_06295_gb300.autograd import kalman_fit
+    g, ev, hits, sp, sc, align, x0, up = _inputs(n=200, seed=23)
+    dev = torch.device("cuda", 0)
+    ctx = make_ctx(g)
+    xyz = f32(ev.hit_xyz.T, dev).requires_grad_(True)
+    al = f32(align, dev).requires_grad_(True)
+    xx = f32(x0, dev).requires_grad_(True)
+    lcov, lay, hd = f32(ev.hit_lcov.T, dev), i32(ev.hit_layer, dev), i32(hits, dev)
+    chi2, par, cov, ok = kalman_fit(ctx, xyz, lcov, lay, hd, f32(sp.T, dev), f32(sc.T, dev), align=al, x0=xx)
+    w = f32(up["g_chi2"], dev)
+    (w * chi2).sum().add(par[3].sum()).backward()
+    T, K = hits.shape
+    ckpt = torch.empty((K, 27, T), dtype=torch.float32, device=dev)
+    mkf.mkf_fit_tracks(ctx, xyz.detach(), lcov, lay, hd, f32(sp.T, dev), f32(sc.T, dev), align=al.detach(),
+                       x0=xx.detach(), ckpt=ckpt)
+    gp = torch.zeros((6, T), dtype=torch.float32, device=dev)
+    gp[3] = 1
+    ref = mkf.mkf_fit_tracks_adjoint(ctx, xyz.detach(), lcov, lay, hd, f32(sp.T, dev), f32(sc.T, dev), ckpt,
+                                     g_chi2=w, g_par=gp, align=al.detach(), x0=xx.detach())
+    mkf.mkf_sync(ctx)
+    assert torch.allclose(xyz.grad, ref["g_hit"], rtol=1e-6, atol=0)
+    assert torch.allclose(al.grad, ref["g_align"], rtol=1e-4, atol=1e-6 * float(ref["g_align"].abs().max()))
+    assert torch.allclose(xx.grad, ref["g_x0"], rtol=1e-4, atol=1e-6 * float(ref["g_x0"].abs().max()))
+    ctx.close()

@@ -1,0 +1,215 @@
+"""Parity of the CUDA building path (through the C ABI) with the FP64 oracle.
+
+Bar: hit assignments, surface sequences and hole counts identical for every
+seed whose decisions are not within 1e-4 (relative) of flipping; parameters
+within 1e-4 relative and covariances within 1e-4 of sqrt(C_ii C_jj)."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from _util import (FRAGILE_TOL, COV_RTOL, PAR_RTOL, compare, gpu_build, i32, i64, f32, make_ctx, oracle_build)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _assert_parity(rep, max_fragile_frac=0.2):
+    print("parity report:", rep)
+    assert rep["mismatch_robust"] == 0, rep
+    assert rep["fragile"] <= max_fragile_frac * rep["n"], rep
+    if "par_err" in rep:
+        assert rep["par_err"] < PAR_RTOL, rep
+        assert rep["cov_err"] < COV_RTOL, rep
+
+
+def test_binning_is_a_stable_sort_by_bin():
+    """perm is a permutation; bin offsets are the exclusive scan of the bin
+    counts; each hit sits in the (event, layer, phi, w) bin of its position
+    (FP64 definition; hits within 1e-5 of a bin edge may sit in either
+    neighbour); inside a bin the original indices ascend."""
+    import paper_2002_06295_gb300 as mkf
+    evs = [synth.make_config_event(2), synth.make_config_event(1)]
+    geom = evs[0].geom
+    dev = torch.device("cuda", 0)
+    nphi, nw = 64, 16
+    ctx = make_ctx(geom, nphi, nw)
+    xyz = np.concatenate([e.hit_xyz for e in evs]); lcov = np.concatenate([e.hit_lcov for e in evs])
+    lay = np.concatenate([e.hit_layer for e in evs])
+    hoff = np.array([0, evs[0].n_hits, evs[0].n_hits + evs[1].n_hits])
+    lay[hoff[1]:] = np.minimum(lay[hoff[1]:], geom.n_layers - 1)
+    mkf.mkf_bin_hits(ctx, f32(xyz.T, dev), f32(lcov.T, dev), i32(lay, dev), i64(hoff, dev))
+    perm, off = mkf.mkf_get_binning(ctx)
+    mkf.mkf_sync(ctx)
+    perm = perm.cpu().numpy(); off = off.cpu().numpy()
+    H = xyz.shape[0]
+    assert np.array_equal(np.sort(perm), np.arange(H))
+    assert off[0] == 0 and off[-1] == H and np.all(np.diff(off) >= 0)
+    B = geom.n_layers * nphi * nw
+    ev = (np.arange(H) >= hoff[1]).astype(np.int64)
+    phi = np.arctan2(xyz[:, 1], xyz[:, 0])
+    r = np.hypot(xyz[:, 0], xyz[:, 1])
+    w = np.where(geom.kind[lay] == 0, xyz[:, 2], r)
+    lo, hi = geom.lo[lay], geom.hi[lay]
+    fp = (phi + np.pi) / (2 * np.pi) * nphi
+    fw = (w - lo) / (hi - lo) * nw
+    ip = np.clip(np.floor(fp), 0, nphi - 1).astype(np.int64)
+    iw = np.clip(np.floor(fw), 0, nw - 1).astype(np.int64)
+    key = ev * B + lay * nphi * nw + ip * nw + iw
+    bin_of_pos = np.repeat(np.arange(len(off) - 1), np.diff(off))
+    got = bin_of_pos[np.argsort(perm)]
+    edge = (np.abs(fp - np.round(fp)) < 1e-5 * nphi) | (np.abs(fw - np.round(fw)) < 1e-5 * nw)
+    bad = (got != key) & ~edge
+    assert bad.sum() == 0
+    for b in np.nonzero(np.diff(off) > 1)[0][:2000]:
+        seg = perm[off[b]:off[b + 1]]
+        assert np.all(np.diff(seg) > 0)
+    ctx.close()
+
+
+@pytest.mark.parametrize("max_cands", [4, 1, 8])
+def test_build_config1_full_event(max_cands):
+    """100-track barrel event: every seed compared, dedup flags included."""
+    ev = synth.make_config_event(1)
+    ctx = make_ctx(ev.geom)
+    g = gpu_build(ctx, [ev], max_cands=max_cands)
+    r = oracle_build([ev], max_cands=max_cands)
+    rep = compare(g, r)
+    _assert_parity(rep)
+    robust = r["margin"] >= FRAGILE_TOL
+    assert np.array_equal(g["flags"][robust], r["flags"][robust])
+    assert g["stats"]["cand_steps"] > 0
+    ctx.close()
+
+
+def test_build_config2_sampled_seeds():
+    """CMS-like 38-surface event at full size (5000 tracks, 85k hits incl. 20 %
+    noise) on the GPU; the oracle builds a sample of 250 seeds against the full
+    hit set and every sampled seed is compared."""
+    ev = synth.make_config_event(2)
+    ctx = make_ctx(ev.geom)
+    g = gpu_build(ctx, [ev], max_cands=6)
+    sel = np.random.default_rng(7).choice(ev.n_seeds, 250, replace=False)
+    r = oracle_build([ev], max_cands=6, seeds=sel, dedup=False)
+    rep = compare(g, r, sel=sel)
+    _assert_parity(rep, max_fragile_frac=0.3)
+    ctx.close()
+
+
+@pytest.mark.parametrize("cfg", [1, 2])
+def test_search_window_is_conservative(cfg):
+    """Debug mode evaluates every hit of the layer: no hit with chi2 < cut may
+    fall outside the binned window."""
+    ev = synth.make_config_event(cfg)
+    ctx = make_ctx(ev.geom)
+    g = gpu_build(ctx, [ev], max_cands=6 if cfg == 2 else 4, debug=True)
+    assert g["stats"]["window_violations"] == 0
+    assert g["stats"]["cand_steps"] > 0
+    ctx.close()
+
+
+def test_batched_events_equal_single_events():
+    """Uneven events in one launch give bit-identical results to one launch per
+    event, and match the oracle per event."""
+    evs = [synth.make_config_event(3, e, n_tracks=n) for e, n in enumerate([5, 300, 1, 120, 40])]
+    ctx = make_ctx(evs[0].geom)
+    g = gpu_build(ctx, evs, max_cands=4)
+    off = 0
+    for i, e in enumerate(evs):
+        s = gpu_build(ctx, [e], max_cands=4)
+        sl = slice(off, off + e.n_seeds)
+        hb = g["hit_off"][i]
+        gh = np.where(g["hits"][sl] >= 0, g["hits"][sl] - hb, -1)
+        assert np.array_equal(gh, s["hits"])
+        assert np.array_equal(g["par"][sl], s["par"])
+        assert np.array_equal(g["flags"][sl], s["flags"])
+        off += e.n_seeds
+    r = oracle_build(evs, max_cands=4)
+    _assert_parity(compare(g, r))
+    ctx.close()
+
+
+def test_empty_and_degenerate_inputs():
+    """An event without hits (every seed ends with only holes), zero seeds, and
+    a hole budget of zero."""
+    import paper_2002_06295_gb300 as mkf
+    ev = synth.make_config_event(1)
+    dev = torch.device("cuda", 0)
+    ctx = make_ctx(ev.geom)
+    # no hits at all
+    mkf.mkf_bin_hits(ctx, torch.zeros((3, 0), dtype=torch.float32, device=dev),
+                     torch.zeros((3, 0), dtype=torch.float32, device=dev),
+                     torch.zeros(0, dtype=torch.int32, device=dev), i64([0, 0], dev))
+    out = mkf.mkf_build_tracks(ctx, f32(ev.seed_par.T, dev), f32(ev.seed_cov.T, dev), i64([0, ev.n_seeds], dev),
+                               max_cands=4, max_holes=3)
+    mkf.mkf_sync(ctx)
+    assert (out["hits"] == -1).all()
+    assert (out["flags"] == mkf.TRK_SHORT).all()
+    assert (out["counts"][0] == 0).all()
+    # zero seeds
+    mkf.mkf_bin_hits(ctx, f32(ev.hit_xyz.T, dev), f32(ev.hit_lcov.T, dev), i32(ev.hit_layer, dev),
+                     i64([0, ev.n_hits], dev))
+    out0 = mkf.mkf_build_tracks(ctx, torch.zeros((6, 0), dtype=torch.float32, device=dev),
+                                torch.zeros((21, 0), dtype=torch.float32, device=dev), i64([0, 0], dev))
+    mkf.mkf_sync(ctx)
+    assert out0["hits"].shape[0] == 0
+    # no holes allowed
+    g = gpu_build(ctx, [ev], max_cands=4, max_holes=0)
+    r = oracle_build([ev], max_cands=4, max_holes=0)
+    _assert_parity(compare(g, r))
+    ctx.close()
+
+
+def test_argument_errors_are_reported():
+    import paper_2002_06295_gb300 as mkf
+    ev = synth.make_config_event(1)
+    dev = torch.device("cuda", 0)
+    ctx = make_ctx(ev.geom)
+    with pytest.raises(mkf.MkfError):
+        mkf.mkf_build_tracks(ctx, f32(ev.seed_par.T, dev), f32(ev.seed_cov.T, dev), i64([0, ev.n_seeds], dev))
+    mkf.mkf_bin_hits(ctx, f32(ev.hit_xyz.T, dev), f32(ev.hit_lcov.T, dev), i32(ev.hit_layer, dev),
+                     i64([0, ev.n_hits], dev))
+    with pytest.raises(mkf.MkfError):
+        mkf.mkf_build_tracks(ctx, f32(ev.seed_par.T, dev), f32(ev.seed_cov.T, dev), i64([0, ev.n_seeds], dev),
+                             max_cands=9)
+    bad = ev.hit_layer.copy()
+    bad[3] = 99
+    mkf.mkf_bin_hits(ctx, f32(ev.hit_xyz.T, dev), f32(ev.hit_lcov.T, dev), i32(bad, dev), i64([0, ev.n_hits], dev))
+    with pytest.raises(mkf.MkfError):
+        mkf.mkf_sync(ctx)
+    ctx.close()
+
+
+def test_dedup_matches_oracle_on_oracle_tracks():
+    """GPU duplicate removal on the oracle's own track list (C1 and a synthetic
+    list with heavy overlaps) gives the oracle's flags exactly."""
+    import oracle
+    import paper_2002_06295_gb300 as mkf
+    dev = torch.device("cuda", 0)
+    ev = synth.make_config_event(1)
+    ref = oracle_build([ev], max_cands=4)
+    ctx = make_ctx(ev.geom)
+    flags = mkf.mkf_dedup_tracks(ctx, i32(ref["hits"], dev), f32(ref["score"], dev), i32(ref["nhits"], dev),
+                                 i64([0, ev.n_seeds], dev), ev.n_hits)
+    mkf.mkf_sync(ctx)
+    assert np.array_equal(flags.cpu().numpy(), ref["flags"])
+    rng = np.random.default_rng(3)
+    S, L, Hn = 3000, 10, 4000
+    hits = np.full((S, L), -1, np.int32)
+    nh = rng.integers(2, L + 1, S)
+    for s in range(S):
+        hits[s, :nh[s]] = rng.choice(Hn, nh[s], replace=False) if rng.random() < 0.5 else \
+            (rng.integers(0, 40) * 100 + rng.choice(60, nh[s], replace=False))
+    score = np.round(rng.normal(30, 10, S), 1).astype(np.float32)   # many exact ties
+    # two events: seeds [0, 1000) and [1000, S); hit ids are disjoint between events
+    hits[1000:] = np.where(hits[1000:] >= 0, hits[1000:] + Hn, -1)
+    flags = mkf.mkf_dedup_tracks(ctx, i32(hits, dev), f32(score, dev), i32(nh, dev), i64([0, 1000, S], dev), 2 * Hn)
+    mkf.mkf_sync(ctx)
+    exp = oracle.dedup(hits, score.astype(np.float64), nh, 4, 0.5)
+    assert np.array_equal(flags.cpu().numpy(), exp)
+    ctx.close()

@@ -1,0 +1,111 @@
+"""Parity of the CUDA fixed-assignment Kalman fit (outward and inward) with the
+FP64 oracle: parameters within 1e-4 relative, covariances within 1e-4 of
+sqrt(C_ii C_jj), chi2 within 1e-4 relative (plus 1e-3 absolute)."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from _util import CHI2_RTOL, COV_RTOL, PAR_RTOL, cov_rel_err, f32, i32, make_ctx, par_rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _fit_inputs(n=2000, seed=11, geom=None):
+    g = geom or synth.geometry_barrel14()
+    rng = np.random.default_rng(seed)
+    ev = synth.simulate_event(g, n, rng, pt_range=(1.0, 10.0), eta_max=0.8)
+    keep = (ev.true_hits >= 0).sum(1) == g.n_layers
+    return g, ev, ev.true_hits[keep], ev.seed_par[keep], ev.seed_cov[keep], rng
+
+
+@pytest.mark.parametrize("with_align", [False, True])
+def test_forward_fit_matches_oracle(with_align):
+    import oracle
+    import paper_2002_06295_gb300 as mkf
+    g, ev, hits, sp, sc, rng = _fit_inputs()
+    align = rng.normal(0, 2e-3, (g.n_layers, 3)) if with_align else None
+    x0 = g.x0 * (1 + 0.2 * rng.random(g.n_layers)) if with_align else None
+    dev = torch.device("cuda", 0)
+    ctx = make_ctx(g)
+    T, K = hits.shape
+    ckpt = torch.empty((K, 27, T), dtype=torch.float32, device=dev)
+    o = mkf.mkf_fit_tracks(ctx, f32(ev.hit_xyz.T, dev), f32(ev.hit_lcov.T, dev), i32(ev.hit_layer, dev),
+                           i32(hits, dev), f32(sp.T, dev), f32(sc.T, dev),
+                           align=None if align is None else f32(align, dev),
+                           x0=None if x0 is None else f32(x0, dev), ckpt=ckpt)
+    mkf.mkf_sync(ctx)
+    par, cov, chi2, ok = oracle.fit(oracle.Geo.of(g), ev.hit_xyz, ev.hit_lcov, ev.hit_layer, hits, sp, sc,
+                                    align=align, x0=x0)
+    gp = o["par"].cpu().numpy().T.astype(np.float64)
+    gc = o["cov"].cpu().numpy().T.astype(np.float64)
+    gx = o["chi2"].cpu().numpy().astype(np.float64)
+    assert (o["ok"].cpu().numpy() == 1).all() and ok.all()
+    pe, ce = par_rel_err(gp, par), cov_rel_err(gc, cov)
+    print("forward fit: par err per parameter", pe.max(0), "cov err", ce.max(),
+          "chi2 rel err", (np.abs(gx - chi2) / chi2).max())
+    assert pe.max() < PAR_RTOL
+    assert ce.max() < COV_RTOL
+    assert (np.abs(gx - chi2) <= CHI2_RTOL * chi2).all()
+    # checkpoint 0 is the initial state
+    ck = ckpt.cpu().numpy()
+    assert np.array_equal(ck[0, :6].T, sp.astype(np.float32))
+    assert np.array_equal(ck[0, 6:].T, sc.astype(np.float32))
+    ctx.close()
+
+
+def test_backward_fit_matches_oracle():
+    import oracle
+    import paper_2002_06295_gb300 as mkf
+    g, ev, hits, sp, sc, rng = _fit_inputs(1500, seed=12)
+    geo = oracle.Geo.of(g)
+    fpar, fcov, _, _ = oracle.fit(geo, ev.hit_xyz, ev.hit_lcov, ev.hit_layer, hits, sp, sc)
+    bpar, bcov, bchi2, bok = oracle.fit(geo, ev.hit_xyz, ev.hit_lcov, ev.hit_layer, hits, fpar, fcov, direction=-1)
+    dev = torch.device("cuda", 0)
+    ctx = make_ctx(g)
+    o = mkf.mkf_fit_backward(ctx, f32(ev.hit_xyz.T, dev), f32(ev.hit_lcov.T, dev), i32(ev.hit_layer, dev),
+                             i32(hits, dev), f32(fpar.T, dev))
+    mkf.mkf_sync(ctx)
+    gp = o["par"].cpu().numpy().T.astype(np.float64)
+    gc = o["cov"].cpu().numpy().T.astype(np.float64)
+    assert bok.all() and (o["ok"].cpu().numpy() == 1).all()
+    pe, ce = par_rel_err(gp, bpar), cov_rel_err(gc, bcov)
+    print("backward fit: par err per parameter", pe.max(0), "cov err", ce.max())
+    assert pe.max() < PAR_RTOL
+    assert ce.max() < COV_RTOL
+    ctx.close()
+
+
+def test_fit_cmslike_mixed_surfaces():
+    """Barrel and disk hits in one track list (CMS-like geometry)."""
+    import oracle
+    import paper_2002_06295_gb300 as mkf
+    g = synth.geometry_cmslike()
+    rng = np.random.default_rng(13)
+    ev = synth.simulate_event(g, 1500, rng, pt_range=(0.8, 20.0), pt_log=True, eta_max=2.4)
+    n = (ev.true_hits >= 0).sum(1)
+    keep = n >= 6
+    hits, sp, sc = ev.true_hits[keep], ev.seed_par[keep], ev.seed_cov[keep]
+    dev = torch.device("cuda", 0)
+    ctx = make_ctx(g)
+    o = mkf.mkf_fit_tracks(ctx, f32(ev.hit_xyz.T, dev), f32(ev.hit_lcov.T, dev), i32(ev.hit_layer, dev),
+                           i32(hits, dev), f32(sp.T, dev), f32(sc.T, dev))
+    mkf.mkf_sync(ctx)
+    par, cov, chi2, ok = oracle.fit(oracle.Geo.of(g), ev.hit_xyz, ev.hit_lcov, ev.hit_layer, hits, sp, sc)
+    gp = o["par"].cpu().numpy().T.astype(np.float64)
+    gc = o["cov"].cpu().numpy().T.astype(np.float64)
+    good = ok.astype(bool) & (o["ok"].cpu().numpy() == 1)
+    assert good.mean() > 0.99
+    pe = par_rel_err(gp[good], par[good])
+    worst = np.argmax(pe.max(1))
+    print("cms-like fit: par err per parameter", pe.max(0), "worst track", gp[good][worst], par[good][worst],
+          hits[good][worst])
+    assert pe.max() < PAR_RTOL
+    assert cov_rel_err(gc[good], cov[good]).max() < COV_RTOL
+    ctx.close()
