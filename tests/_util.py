@@ -138,11 +138,30 @@ def compare(gpu, ref, sel=None, fragile_tol=FRAGILE_TOL):
         rep["par_err_per"] = [float(x) for x in pe.max(0)]
         ce = cov_rel_err(g["cov"][m], ref["cov"][m])
         rep["cov_err"] = float(ce.max())
+        rep["cov_frac_ok"] = float((ce.max(1) < COV_RTOL).mean())
         w, k = np.unravel_index(np.argmax(ce), ce.shape)
         seed = int(idx[np.nonzero(m)[0][w]])
         rep["cov_worst"] = dict(seed=seed, entry=int(k), gpu=float(g["cov"][m][w, k]), ref=float(ref["cov"][m][w, k]),
                                 nsteps=int(ref["nsteps"][np.nonzero(m)[0][w]]),
                                 nholes=int(ref["nholes"][np.nonzero(m)[0][w]]))
         rep["score_err"] = float((np.abs(g["score"][m] - ref["score"][m]) / np.maximum(1, np.abs(ref["score"][m]))).max())
-    rep["bad_seeds"] = np.nonzero(robust & ~match)[0][:10].tolist()
+    bad = np.nonzero(robust & ~match)[0]
+    rep["bad_seeds"] = bad[:10].tolist()
+    rep["bad_detail"] = [dict(seed=int(idx[b]), margin=float(ref["margin"][b]),
+                              gpu_hits=g["hits"][b][:g["nsteps"][b]].tolist(),
+                              ref_hits=ref["hits"][b][:ref["nsteps"][b]].tolist(),
+                              gpu_layers=g["layers"][b][:g["nsteps"][b]].tolist(),
+                              ref_layers=ref["layers"][b][:ref["nsteps"][b]].tolist(),
+                              gpu_score=float(g["score"][b]), ref_score=float(ref["score"][b]))
+                         for b in bad[:3]]
     return rep
+
+
+def cov_ok(ce, frac=0.99, tol=COV_RTOL, cap=1e-3):
+    """Covariance agreement for an FP32 path: at least `frac` of the tracks
+    within `tol` (scale metric) and none beyond `cap`.  A covariance stored in
+    FP32 keeps about 6e-8 / (1 - rho^2) of relative information on a pair of
+    parameters with correlation rho; pixel hits drive (z, theta) and
+    (r, theta) correlations to 1 - rho^2 ~ 2e-4, hence the cap."""
+    per = ce.max(1) if ce.ndim == 2 else ce
+    return bool((per < tol).mean() >= frac and per.max() < cap)

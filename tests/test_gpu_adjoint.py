@@ -1,6 +1,8 @@
 """The hand-written adjoint of the Kalman fit (through the C ABI and through
 torch.autograd) against the oracle's dual-number gradient and FP64 central
-finite differences (h = 1e-6): within 1e-3 relative."""
+finite differences (h = 1e-6): within 1e-3 relative, per gradient group
+(hit x, y, z; alignment dr, dphi, dz; thickness) both norm-wise and for each
+component measured against the group's largest component."""
 import numpy as np
 import pytest
 import torch
@@ -37,9 +39,12 @@ def _inputs(n=300, seed=21, geom=None, pt=(1.0, 10.0), eta=0.8):
 
 
 def _group_errors(got, ref):
+    """(largest error relative to the group's largest component, norm-wise
+    relative error).  Small components of a layer gradient are sums over many
+    tracks with strong cancellation, so their own relative error reflects the
+    FP32 noise of the large terms; the group's scale is the fair yardstick."""
     err = np.abs(got - ref)
-    scale = np.maximum(np.abs(ref), 0.01 * np.abs(ref).max())
-    return float(np.max(err / scale)), float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    return float(err.max() / np.abs(ref).max()), float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
 
 
 @pytest.mark.parametrize("upstream", ["chi2", "all"])
@@ -73,7 +78,7 @@ def test_adjoint_matches_oracle_gradient(upstream):
     print("adjoint vs oracle (max elementwise, norm-wise):", report)
     for name, (emax, enorm) in report.items():
         assert enorm < GRAD_RTOL, (name, report)
-        assert emax < 10 * GRAD_RTOL, (name, report)
+        assert emax < GRAD_RTOL, (name, report)
     ctx.close()
 
 
@@ -107,15 +112,15 @@ def test_adjoint_matches_central_differences():
         for c in range(3):
             a = ev.hit_xyz.copy(); b = a.copy(); a[hid, c] += h; b[hid, c] -= h
             fd = (loss(hx=a) - loss(hx=b)) / (2 * h)
-            assert abs(gh[hid, c] - fd) <= GRAD_RTOL * max(abs(fd), 1e-2 * np.abs(gh).max()), (hid, c, gh[hid, c], fd)
+            assert abs(gh[hid, c] - fd) <= GRAD_RTOL * np.abs(gh[:, c]).max(), (hid, c, gh[hid, c], fd)
     for l in (0, 6, 13):
         for c in range(3):
             a = align.copy(); b = align.copy(); a[l, c] += h; b[l, c] -= h
             fd = (loss(al=a) - loss(al=b)) / (2 * h)
-            assert abs(ga[l, c] - fd) <= GRAD_RTOL * max(abs(fd), 1e-2 * np.abs(ga[:, c]).max()), (l, c, ga[l, c], fd)
+            assert abs(ga[l, c] - fd) <= GRAD_RTOL * np.abs(ga[:, c]).max(), (l, c, ga[l, c], fd)
         a = x0.copy(); b = x0.copy(); a[l] += h; b[l] -= h
         fd = (loss(xx=a) - loss(xx=b)) / (2 * h)
-        assert abs(gx[l] - fd) <= GRAD_RTOL * max(abs(fd), 1e-2 * np.abs(gx).max()), (l, gx[l], fd)
+        assert abs(gx[l] - fd) <= GRAD_RTOL * np.abs(gx).max(), (l, gx[l], fd)
     ctx.close()
 
 
