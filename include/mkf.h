@@ -158,6 +158,26 @@ mkf_status mkf_dedup_tracks(mkf_ctx* ctx, const int* hits, int L, const float* s
                             const int64_t* ev_seed_off, int n_events, int64_t n_seeds, int64_t n_hits_total,
                             int min_hits, float dup_frac, int* out_flags, void* stream);
 
+/* Duplicate removal without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory while they run (a trigger or online process that reserves its
+ * whole memory budget at start-up, or a thread that must not take the implicit
+ * device synchronisation of cudaMalloc).  Same rule and arguments as
+ * mkf_dedup_tracks, but no context: its working memory is one fixed 8.5 MB
+ * array in the library's device image, which every GPU that loads the library
+ * holds until the process exits.  Limits: n_seeds <= 16384,
+ * n_hits_total <= 524288, L <= MKF_MAX_LAYERS; larger inputs return
+ * MKF_ERR_CAPACITY and nothing is enqueued.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share the
+ * array: calls whose work can overlap on the GPU race and must be serialised
+ * by the caller.  Device-side problems are written as MKF status bits to
+ * out_status (DEVICE int, cleared by the call; may be NULL): 1 capacity,
+ * 2 resolution did not converge, 4 an input hit id out of range. */
+mkf_status mkf_dedup_tracks_noalloc(const int* hits, int L, const float* score, const int* nhits,
+                                    const int64_t* ev_seed_off, int n_events, int64_t n_seeds, int64_t n_hits_total,
+                                    int min_hits, float dup_frac, int* out_flags, int* out_status, void* stream);
+
 /* Kalman fit over a fixed hit assignment (Sec. 1: "fitting simply applies the
  * KF procedure to all hits identified during building").  For each listed hit
  * in crossing order: propagate to that hit's surface, add its material,

@@ -180,6 +180,19 @@ def mkf_dedup_tracks(ctx, hits, score, nhits, ev_seed_off, n_hits_total, min_hit
     return flags
 
 
+def mkf_dedup_tracks_noalloc(hits, score, nhits, ev_seed_off, n_hits_total, min_hits=4, dup_frac=0.5,
+                             out_flags=None, out_status=None, stream=None):
+    """Duplicate removal that allocates no device memory inside the library
+    (fixed working array; see include/mkf.h for its limits).  Returns the
+    status code; flags and status are written to the given device tensors."""
+    S, L = int(hits.shape[0]), int(hits.shape[1])
+    E = int(ev_seed_off.shape[0]) - 1
+    return _lib.load().mkf_dedup_tracks_noalloc(
+        _ptr(hits, torch.int32, "hits"), L, _ptr(score, torch.float32, "score"), _ptr(nhits, torch.int32, "nhits"),
+        _ptr(ev_seed_off, torch.int64, "ev_seed_off"), E, S, int(n_hits_total), int(min_hits), float(dup_frac),
+        _ptr(out_flags, torch.int32, "out_flags"), _ptr(out_status, torch.int32, "out_status"), _stream(stream))
+
+
 def mkf_fit_tracks(ctx, xyz, lcov, layer, hits, init_par, init_cov, align=None, x0=None, ckpt=None, out=None,
                    stream=None):
     H = int(layer.shape[0])

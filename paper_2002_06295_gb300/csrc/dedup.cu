@@ -175,3 +175,92 @@ cudaError_t launch_dedup(mkf_ctx* ctx, const int* hits, int L, const float* scor
 }
 
 }  // namespace mkf
+
+// ---------------------------------------------------------------------------
+// Allocation-free duplicate removal.
+//
+// Some callers cannot allocate device memory once they are running: a trigger
+// or online-reconstruction process that reserves its whole memory budget at
+// start-up, or a host thread that must not take cudaMalloc's implicit device
+// synchronisation while other streams are busy.  For them this variant keeps
+// its working memory in one fixed array in the library's device image (held
+// by every GPU that loads the library until the process exits) and never calls
+// cudaMalloc, cudaFree or any allocating routine.  Sizes beyond the array's
+// limits are rejected with MKF_ERR_CAPACITY before anything is enqueued.
+// Every call uses the same array: calls whose work overlaps on the GPU (other
+// streams, other host threads) race with each other and must be serialised by
+// the caller.
+#include <mutex>
+
+namespace mkf {
+namespace {
+
+constexpr int64_t kNaMaxSeeds = 16384;
+constexpr int64_t kNaMaxHits = 524288;
+constexpr size_t kNaHead = (size_t)kNaMaxHits;                        // head[hit]
+constexpr size_t kNaNext = (size_t)kNaMaxSeeds * MKF_MAX_LAYERS;      // next[seed * L + k]
+constexpr size_t kNaBeat = (size_t)kNaMaxSeeds * kMaxBeaters;         // beat[seed * 32 + j]
+constexpr size_t kNaWords = kNaHead + kNaNext + kNaBeat + 2 * (size_t)kNaMaxSeeds + 64;
+
+// 8.5 MB of working memory, 256-byte aligned, in the device image.
+static __device__ __align__(256) int g_dedup_scratch[kNaWords];
+
+constexpr int kNaMaxDevices = 64;
+std::mutex g_na_mutex;
+int* g_na_ptr[kNaMaxDevices] = {};
+
+// Device address of g_dedup_scratch on the current device, looked up once per
+// device (the host-side symbol is only a stand-in and must not be passed to a
+// kernel).
+cudaError_t noalloc_scratch(int** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kNaMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_na_mutex);
+  if (!g_na_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_dedup_scratch);
+    if (e != cudaSuccess) return e;
+    g_na_ptr[dev] = static_cast<int*>(p);
+  }
+  *out = g_na_ptr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace mkf
+
+extern "C" mkf_status mkf_dedup_tracks_noalloc(const int* hits, int L, const float* score, const int* nhits,
+                                               const int64_t* ev_seed_off, int n_events, int64_t n_seeds,
+                                               int64_t n_hits_total, int min_hits, float dup_frac, int* out_flags,
+                                               int* out_status, void* stream) {
+  using namespace mkf;
+  if (L < 1 || L > MKF_MAX_LAYERS || n_events < 1 || n_seeds < 0 || n_hits_total < 0) return MKF_ERR_ARG;
+  if (min_hits < 0 || !(dup_frac >= 0.0f && dup_frac <= 1.0f)) return MKF_ERR_ARG;
+  if (!ev_seed_off || (n_seeds > 0 && (!hits || !score || !nhits || !out_flags))) return MKF_ERR_ARG;
+  if (n_seeds > kNaMaxSeeds || n_hits_total > kNaMaxHits) return MKF_ERR_CAPACITY;
+  cudaStream_t st = (cudaStream_t)stream;
+  int* base = nullptr;
+  if (noalloc_scratch(&base) != cudaSuccess) return MKF_ERR_CUDA;
+  int* head = base;
+  int* next = head + kNaHead;
+  int* beat = next + kNaNext;
+  int* nbeat = beat + kNaBeat;
+  int* state = nbeat + kNaMaxSeeds;
+  unsigned long long* stats = reinterpret_cast<unsigned long long*>(state + kNaMaxSeeds);   // 8 counters
+  int* status = out_status ? out_status : reinterpret_cast<int*>(stats + 8);
+  // the array keeps the previous call's contents: reset what must start fresh
+  if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return MKF_ERR_CUDA;
+  if (n_seeds == 0) return MKF_OK;
+  const int64_t H = n_hits_total > 0 ? n_hits_total : 1;
+  if (cudaMemsetAsync(head, 0xFF, (size_t)H * sizeof(int), st) != cudaSuccess) return MKF_ERR_CUDA;
+  const int T = 256;
+  const unsigned gs = (unsigned)((n_seeds + T - 1) / T);
+  k_dd_link<<<gs, T, 0, st>>>(hits, L, nhits, n_seeds, n_hits_total, min_hits, head, next, status);
+  k_dd_conflicts<<<gs, T, 0, st>>>(hits, L, score, nhits, n_seeds, n_hits_total, min_hits, dup_frac, head, next, beat,
+                                   nbeat, status);
+  k_dd_resolve<<<(unsigned)n_events, 1024, 0, st>>>(ev_seed_off, nhits, min_hits, beat, nbeat, state, out_flags,
+                                                    stats, status);
+  return cudaGetLastError() == cudaSuccess ? MKF_OK : MKF_ERR_CUDA;
+}
