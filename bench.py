@@ -33,12 +33,13 @@ WORKLOAD = "C2 CMS-like event: 38 surfaces (14 barrel + 24 disk), 5000 tracks, ~
 METRIC = "candidate Kalman steps/s"
 UNIT = "cand-steps/s"
 
-# FP32 work per unit, counted from the kernel formulas (FMA = 2, add/mul = 1;
-# sqrt, rcp, sin/cos, atan, log counted separately as SFU): see the design doc
-FLOPS_NAV_TEST = 50       # one surface tested by the navigation (path + acceptance)
-FLOPS_CAND_STEP = 480     # propagate + Jacobian + J C J^T + material + window
-FLOPS_CHI2 = 32           # one candidate-hit chi2
-FLOPS_UPDATE = 198        # one Kalman update of a kept child
+# FP32 work per unit, counted from the kernel formulas as executed (FMA = 2,
+# add/mul/div = 1; sqrt, rsqrt, sin/cos, atan, log not counted); barrel-surface
+# counts, so disk-heavy work is under-counted
+FLOPS_NAV_TEST = 44       # one surface tested by the navigation (crossing path + acceptance)
+FLOPS_CAND_STEP = 600     # helix 46 + Jacobian 84 + J C J^T 408 + material 25 + window ~35
+FLOPS_CHI2 = 40           # one candidate-hit chi2 (with the Cauchy-Schwarz floor)
+FLOPS_UPDATE = 625        # one Kalman update of a kept child, Joseph-form covariance
 FP32_LANES = 128          # per SM (Blackwell)
 
 
@@ -223,19 +224,18 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = n_cores()
         pool = oracle_pool(cores)
-        per = args.cpu_sample_seeds or 40 * cores
+        per = args.cpu_sample_seeds or 5000
         u, dt = oracle_step(pool, cores, per, 0)
         pool.close()
         cpu = {"value": u / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": "%d of the 5000 seeds of the C2 event (building only, brute-force hit search), "
-                         "one process per core, %.1f s" % (per, dt)}
+               "sample": "%d of the 5000 seeds of the C2 event (building only, FP64, brute-force hit search), "
+                         "one process per core, %.1f s wall" % (per, dt)}
 
     dev = torch.device("cuda", local)
     ev = synth.make_config_event(2, rank)
     g = ev.geom
     ctx = mkf.Context(local)
     mkf.mkf_load_geometry(ctx, g.table(), g.bz, 64, 16)
-    mkf.mkf_set_timing(ctx, True)
     spec = synth.CONFIGS[2]
     f32 = dict(dtype=torch.float32)
     host = dict(xyz=torch.tensor(ev.hit_xyz.T.copy(), **f32), lcov=torch.tensor(ev.hit_lcov.T.copy(), **f32),
@@ -245,6 +245,11 @@ def main():
                 soff=torch.tensor([0, ev.n_seeds], dtype=torch.int64))
     host = {k: v.pin_memory() for k, v in host.items()}
     d = {k: v.to(dev) for k, v in host.items()}
+    # launch shape and bin granularity picked on this event (not timed)
+    from paper_2002_06295_gb300 import tune
+    tuned = tune.autotune_build(ctx, g.table(), g.bz, d["xyz"], d["lcov"], d["layer"], d["hoff"], d["sp"], d["sc"],
+                                d["soff"], max_cands=spec["max_cands"], chi2_cut=spec["chi2_cut"],
+                                max_holes=spec["max_holes"], min_hits=spec["min_hits"], dup_frac=spec["dup_frac"])
     S, L = ev.n_seeds, g.n_layers
     out = mkf.alloc_build_outputs(ctx, S)
     ckpt = torch.empty((L, 27, S), dtype=torch.float32, device=dev)
@@ -257,6 +262,7 @@ def main():
                    g_x0=torch.empty(L, device=dev))
     has_adjoint = [True]
     stream = torch.cuda.current_stream()
+    mkf.mkf_set_timing(ctx, True)
 
     def step(inp):
         mkf.mkf_bin_hits(ctx, inp["xyz"], inp["lcov"], inp["layer"], inp["hoff"])
@@ -353,7 +359,8 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "events_per_step_per_gpu": 1, "tracks": S, "hits": ev.n_hits,
                    "surfaces": L, "max_cands": spec["max_cands"], "l2": "flushed (256 MB write) between timed steps",
-                   "adjoint_in_step": has_adjoint[0]},
+                   "adjoint_in_step": has_adjoint[0],
+                   "tuned": {k: tuned[k] for k in ("n_phi", "n_w", "warps", "lanes")}},
         "events_per_s": world * args.steps / (total_ms * 1e-3),
         "fit_tracks_per_s": world * S * args.steps / (total_ms * 1e-3),
         "stage_ms": {"bin": statistics.mean(bin_ms), "build": b_ms, "dedup": statistics.mean(dd_ms),

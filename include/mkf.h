@@ -131,6 +131,13 @@ mkf_status mkf_build_tracks(mkf_ctx* ctx, const float* seed_par, const float* se
                             float dup_frac, int* out_hits, int* out_layers, float* out_par, float* out_cov,
                             float* out_score, float* out_chi2, int* out_counts, int* out_flags, void* stream);
 
+/* Launch shape of the building kernel: warps per thread block (1, 2, 4 or 8;
+ * default 4) and lanes per seed (a power of two up to 32, at least max_cands;
+ * 0 = max_cands rounded up).  More lanes per seed shorten the search of wide
+ * windows, fewer keep more seeds in flight.  Chosen by the autotuner
+ * (paper_2002_06295_gb300/tune.py); it changes speed only, never results. */
+mkf_status mkf_set_build_config(mkf_ctx* ctx, int warps_per_block, int lanes_per_seed);
+
 /* Debug switch for mkf_build_tracks: when on, every candidate step also
  * evaluates chi2 against every hit of the layer and counts accepted hits that
  * lay outside its search window (statistic 4 of mkf_get_stats; it must be 0). */

@@ -140,6 +140,10 @@ def mkf_build_tracks(ctx, seed_par, seed_cov, ev_seed_off, chi2_cut=30.0, max_ca
     return o
 
 
+def mkf_set_build_config(ctx, warps_per_block=4, lanes_per_seed=0):
+    ctx._check(ctx.lib.mkf_set_build_config(ctx.h, int(warps_per_block), int(lanes_per_seed)), "mkf_set_build_config")
+
+
 def mkf_set_debug(ctx, brute_force_window_check):
     ctx._check(ctx.lib.mkf_set_debug(ctx.h, int(bool(brute_force_window_check))), "mkf_set_debug")
 

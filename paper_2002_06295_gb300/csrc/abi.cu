@@ -184,6 +184,18 @@ mkf_status mkf_build_tracks(mkf_ctx* ctx, const float* seed_par, const float* se
   return MKF_OK;
 }
 
+mkf_status mkf_set_build_config(mkf_ctx* ctx, int warps_per_block, int lanes_per_seed) {
+  if (check_ctx(ctx)) return MKF_ERR_ARG;
+  if (warps_per_block != 1 && warps_per_block != 2 && warps_per_block != 4 && warps_per_block != 8)
+    return ctx->fail(MKF_ERR_ARG, "warps_per_block must be 1, 2, 4 or 8");
+  if (lanes_per_seed != 0 && lanes_per_seed != 1 && lanes_per_seed != 2 && lanes_per_seed != 4 &&
+      lanes_per_seed != 8 && lanes_per_seed != 16 && lanes_per_seed != 32)
+    return ctx->fail(MKF_ERR_ARG, "lanes_per_seed must be 0 or a power of two up to 32");
+  ctx->build_warps = warps_per_block;
+  ctx->build_group = lanes_per_seed;
+  return MKF_OK;
+}
+
 mkf_status mkf_set_debug(mkf_ctx* ctx, int brute_force_window_check) {
   if (check_ctx(ctx)) return MKF_ERR_ARG;
   ctx->debug_window = brute_force_window_check ? 1 : 0;

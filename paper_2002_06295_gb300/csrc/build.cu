@@ -11,14 +11,19 @@
 // finished candidate is the seed's track.
 //
 // GB300 mapping:
-//  * a seed is owned by a group of N = max_cands consecutive lanes of a warp;
-//    lane k of the group holds candidate slot k (27 floats in registers);
-//  * groups take seeds from a global queue (atomic counter) and refill as soon
-//    as their seed is done, so one launch covers many events of uneven size;
-//  * each lane keeps its own best children (sorted 64-bit keys) while it scans
-//    its window; the group merges them with N rounds of shuffle min-reductions;
+//  * a seed is owned by a group of GS consecutive lanes of a warp (GS a power
+//    of two >= N = max_cands, chosen per workload); lane k < N of the group
+//    holds candidate slot k (27 floats in registers) for navigation,
+//    propagation, J C J^T and material;
+//  * all GS lanes then scan every candidate's search window together (hits
+//    strided over the lanes), so a wide window -- the seed's first layers --
+//    is shared instead of serialised on one lane; each lane keeps its own best
+//    children (sorted 64-bit keys carrying the parent slot) and the group
+//    merges them with N rounds of shuffle min-reductions;
 //  * only the selected children are Kalman-updated (the score needs only the
 //    predicted chi2), reading the parent's propagated state from shared memory;
+//  * groups take seeds from a global queue (atomic counter) and refill as soon
+//    as their seed is done, so one launch covers many events of uneven size;
 //  * the parent pointers and hits of every step stay in shared memory and are
 //    walked back once per seed.
 #include "mkf_device.cuh"
@@ -28,9 +33,9 @@ namespace mkf {
 
 namespace {
 
-constexpr int kWarps = 4;
-constexpr int kThreads = kWarps * 32;
-constexpr int kSlotWords = 32;             // per-lane shared slot: p[6], C[21], score, nh, nholes, rho, zeta
+constexpr int kMaxWarps = 8;
+constexpr int kSlotWords = 32;             // per-lane shared slot: p[6], C[21], score, nh, nholes|layer, rho, zeta
+constexpr int kWinWords = 8;               // per-lane window: kind, base bin, nphi, nw, b0, nb, iw0, iw1
 constexpr uint32_t kHoleKey = 0x0FFFFFFFu;
 constexpr uint32_t kHistHole = 0x3FFFFFu;  // 22-bit local hit index field
 
@@ -51,6 +56,7 @@ struct BuildDev {
   int n_events;
   float chi2_cut;
   int ncand;
+  int gsize;          // lanes per seed: a power of two >= ncand, <= 32
   int max_holes;
   int debug;
   int* out_hits;
@@ -105,28 +111,38 @@ __device__ __forceinline__ int event_of(const int64_t* off, int n_events, int64_
   return lo;
 }
 
-// min over the N lanes of a group (cyclic shifts 1, 2, 4 cover N <= 8)
-__device__ __forceinline__ uint64_t group_min(uint64_t v, int gbase, int li, int N) {
-  for (int off = 1; off < N; off <<= 1) {
-    int p = li + off;
-    if (p >= N) p -= N;
-    uint64_t o = __shfl_sync(0xffffffffu, v, gbase + p);
+// min / max over the GS lanes of a group (GS a power of two, groups aligned)
+__device__ __forceinline__ uint64_t group_min(uint64_t v, int GS) {
+  for (int off = 1; off < GS; off <<= 1) {
+    const uint64_t o = __shfl_xor_sync(0xffffffffu, v, off);
     v = o < v ? o : v;
   }
   return v;
 }
-__device__ __forceinline__ uint64_t group_max(uint64_t v, int gbase, int li, int N) {
-  for (int off = 1; off < N; off <<= 1) {
-    int p = li + off;
-    if (p >= N) p -= N;
-    uint64_t o = __shfl_sync(0xffffffffu, v, gbase + p);
+__device__ __forceinline__ uint64_t group_max(uint64_t v, int GS) {
+  for (int off = 1; off < GS; off <<= 1) {
+    const uint64_t o = __shfl_xor_sync(0xffffffffu, v, off);
     v = o > v ? o : v;
   }
   return v;
 }
 
+template <int NMAX> __device__ __forceinline__ void insert_child(uint64_t keys[NMAX], int kpos[NMAX], uint64_t kk, int kp) {
+#pragma unroll
+  for (int j = 0; j < NMAX; ++j) {
+    if (kk < keys[j]) {
+      const uint64_t tk = keys[j];
+      keys[j] = kk;
+      kk = tk;
+      const int tp = kpos[j];
+      kpos[j] = kp;
+      kp = tp;
+    }
+  }
+}
+
 template <int NMAX>
-__global__ void __launch_bounds__(kThreads) k_build(const BuildDev a) {
+__global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
   extern __shared__ __align__(16) unsigned char smem[];
   GeomDev& G = *reinterpret_cast<GeomDev*>(smem);
   {
@@ -135,23 +151,32 @@ __global__ void __launch_bounds__(kThreads) k_build(const BuildDev a) {
     for (int i = threadIdx.x; i < (int)(sizeof(GeomDev) / 16); i += blockDim.x) dst[i] = src[i];
   }
   __syncthreads();
+  const int W = blockDim.x >> 5;
   const int L = G.n_layers;
   const int N = a.ncand;
-  const int NG = 32 / N;                      // groups per warp
+  const int GS = a.gsize;                     // lanes per seed (candidates on lanes 0..N-1)
+  const int NG = 32 / GS;                     // groups per warp
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  const int gi = lane / N;
-  const int li = lane - gi * N;
-  const bool gvalid = gi < NG;
-  const int gbase = gi * N;
-  const unsigned gmask = gvalid ? (((1u << N) - 1u) << gbase) : 0u;
+  const int gi = lane / GS;
+  const int li = lane - gi * GS;
+  const bool gvalid = true;
+  const int gbase = gi * GS;
+  const unsigned gmask = (GS == 32 ? 0xffffffffu : ((1u << GS) - 1u)) << gbase;
 
-  float* slots = reinterpret_cast<float*>(smem + sizeof(GeomDev));                 // [kWarps][32][kSlotWords]
-  constexpr int NGM = max_groups<NMAX>();
-  float* bests = slots + kWarps * 32 * kSlotWords;                                  // [kWarps][NGM][32]
-  uint32_t* hist = reinterpret_cast<uint32_t*>(bests + kWarps * NGM * 32);          // [kWarps][NGM][L][NMAX]
-  float* myslot = slots + (warp * 32 + lane) * kSlotWords;
-  float* gslots = slots + (warp * 32 + gbase) * kSlotWords;
+  const int NGM = NG;
+  float* pre = reinterpret_cast<float*>(smem + sizeof(GeomDev));                   // [W][32][kSlotWords]
+  float* prop = pre + W * 32 * kSlotWords;                                          // [W][32][kSlotWords]
+  int* win = reinterpret_cast<int*>(prop + W * 32 * kSlotWords);                   // [W][32][kWinWords]
+  int* cnt = win + W * 32 * kWinWords;                                              // [W][32]
+  float* bests = reinterpret_cast<float*>(cnt + W * 32);                            // [W][NGM][32]
+  uint32_t* hist = reinterpret_cast<uint32_t*>(bests + W * NGM * 32);               // [W][NGM][L][NMAX]
+  float* mypre = pre + (warp * 32 + lane) * kSlotWords;
+  float* myprop = prop + (warp * 32 + lane) * kSlotWords;
+  float* gprop = prop + (warp * 32 + gbase) * kSlotWords;
+  int* mywin = win + (warp * 32 + lane) * kWinWords;
+  int* gwin = win + (warp * 32 + gbase) * kWinWords;
+  int* gcnt = cnt + warp * 32 + gbase;
   float* best = bests + (warp * NGM + (gvalid ? gi : 0)) * 32;
   uint32_t* ghist = hist + (size_t)(warp * NGM + (gvalid ? gi : 0)) * L * NMAX;
 
@@ -206,14 +231,12 @@ __global__ void __launch_bounds__(kThreads) k_build(const BuildDev a) {
     // ---- (0) save the pre-step state: finished candidates are read back from here
     if (active) {
 #pragma unroll
-      for (int k = 0; k < 6; ++k) myslot[k] = p[k];
+      for (int k = 0; k < 6; ++k) mypre[k] = p[k];
 #pragma unroll
-      for (int k = 0; k < 21; ++k) myslot[6 + k] = C[k];
-      myslot[27] = score;
-      myslot[28] = __int_as_float(nh);
-      myslot[29] = __int_as_float(nholes);
-      myslot[30] = rho;
-      myslot[31] = zeta;
+      for (int k = 0; k < 21; ++k) mypre[6 + k] = C[k];
+      mypre[27] = score;
+      mypre[28] = __int_as_float(nh);
+      mypre[29] = __int_as_float(nholes);
     }
     // ---- (1) navigation: next reachable surface outward
     int nl = -1;
@@ -267,20 +290,14 @@ __global__ void __launch_bounds__(kThreads) k_build(const BuildDev a) {
         }
       }
     }
-    // ---- (2) propagate, transport the covariance, material; (3) window scan
-    uint64_t keys[NMAX];
-    int kpos[NMAX];
-#pragma unroll
-    for (int k = 0; k < NMAX; ++k) {
-      keys[k] = ~0ull;
-      kpos[k] = -1;
-    }
-    int nk = 0;
-    int kind = 0;
+    // ---- (2) propagate, transport the covariance, add material, build the
+    // window, and publish the propagated state and window for the group
+    bool hole_ok = false;
+    mywin[5] = 0;
     if (nl >= 0) {
       ++n_steps;
       const LayerDev ly = G.L[nl];
-      kind = ly.kind;
+      const int kind = ly.kind;
       const auto h = helix_at(p[0], p[1], p[2], p[4], cot_t, omega, ns);
       const auto J = transport_jacobian(kind, p, h, ns, omega, ck, cot_t, sin_t);
       similarity(J, C);
@@ -290,8 +307,6 @@ __global__ void __launch_bounds__(kThreads) k_build(const BuildDev a) {
       p[4] = wrap_phi(h.phi);
       add_material(kind, ly.x0, h.x, h.y, h.cphi, h.sphi, p[3], sin_t, cos_t, C);
       const float rc = sqrtf(fmaf(h.x, h.x, h.y * h.y));
-      const float nrho = kind == 0 ? ly.pos : fmaxf(rho, rc);
-      const float nzeta = kind == 0 ? fmaxf(zeta, fabsf(h.z)) : fabsf(ly.pos);
       // conservative window: |r_i| < sqrt(cut R_ii) (Cauchy-Schwarz), R_ii bounded
       // by the largest eigenvalue of C_xy (or C_zz) plus the layer's largest hit variance
       const float va = __ldg(&a.vmax[2 * (ev * L + nl)]);
@@ -304,13 +319,8 @@ __global__ void __launch_bounds__(kThreads) k_build(const BuildDev a) {
       const float phic = atan2f(h.y, h.x);
       float dphi = ha >= rc ? 0.5f * kPi : asinf(ha / rc);
       dphi = dphi * 1.001f + 1e-5f;
-      int b0, nb;
-      {
-        const float lo_f = floorf((phic - dphi + kPi) * ly.phi_scale);
-        const float hi_f = floorf((phic + dphi + kPi) * ly.phi_scale);
-        b0 = (int)lo_f;
-        nb = min((int)(hi_f - lo_f) + 1, ly.nphi);
-      }
+      const float lo_f = floorf((phic - dphi + kPi) * ly.phi_scale);
+      const float hi_f = floorf((phic + dphi + kPi) * ly.phi_scale);
       float wlo, whi;
       if (kind == 0) {
         wlo = h.z - hb;
@@ -319,95 +329,99 @@ __global__ void __launch_bounds__(kThreads) k_build(const BuildDev a) {
         wlo = fmaf(rc, cosf(fminf(dphi, 0.5f * kPi)), -hb);
         whi = rc + hb;
       }
-      const int iw0 = min(max((int)floorf((wlo - ly.lo) * ly.w_scale), 0), ly.nw - 1);
-      const int iw1 = min(max((int)floorf((whi - ly.lo) * ly.w_scale), 0), ly.nw - 1);
-      const int base = ebin + ly.bin_base;
-      for (int k = 0; k < nb; ++k) {
-        int b = (b0 + k) % ly.nphi;
-        if (b < 0) b += ly.nphi;
-        const int beg = __ldg(&a.bin_off[base + b * ly.nw + iw0]);
-        const int end = __ldg(&a.bin_off[base + b * ly.nw + iw1 + 1]);
-        for (int q = beg; q < end; ++q) {
-          const HitRec hr = load_rec(a.rec, q);
-          const float chi2 = hit_chi2(kind, p, C, hr);
-          ++n_chi2;
-          if (chi2 < cut) {
-            uint64_t kk = child_key(score + 10.0f - chi2, li, (uint32_t)hr.orig);
-            int kp = q;
+      mywin[0] = kind;
+      mywin[1] = ebin + ly.bin_base;
+      mywin[2] = ly.nphi;
+      mywin[3] = ly.nw;
+      mywin[4] = (int)lo_f;
+      mywin[5] = max(min((int)(hi_f - lo_f) + 1, ly.nphi), 1);
+      mywin[6] = min(max((int)floorf((wlo - ly.lo) * ly.w_scale), 0), ly.nw - 1);
+      mywin[7] = min(max((int)floorf((whi - ly.lo) * ly.w_scale), 0), ly.nw - 1);
 #pragma unroll
-            for (int j = 0; j < NMAX; ++j) {
-              if (kk < keys[j]) {
-                uint64_t tk = keys[j];
-                keys[j] = kk;
-                kk = tk;
-                int tp = kpos[j];
-                kpos[j] = kp;
-                kp = tp;
-              }
+      for (int k = 0; k < 6; ++k) myprop[k] = p[k];
+#pragma unroll
+      for (int k = 0; k < 21; ++k) myprop[6 + k] = C[k];
+      myprop[27] = score;
+      myprop[28] = __int_as_float(nh);
+      myprop[29] = __int_as_float(nholes | (nl << 16));
+      myprop[30] = kind == 0 ? ly.pos : fmaxf(rho, rc);
+      myprop[31] = kind == 0 ? fmaxf(zeta, fabsf(h.z)) : fabsf(ly.pos);
+      hole_ok = nholes + 1 <= a.max_holes;
+    }
+    cnt[warp * 32 + lane] = 0;
+    __syncwarp();
+    // ---- (3) the group scans each candidate's window together
+    uint64_t keys[NMAX];
+    int kpos[NMAX];
+#pragma unroll
+    for (int k = 0; k < NMAX; ++k) {
+      keys[k] = ~0ull;
+      kpos[k] = -1;
+    }
+    if (gvalid) {
+      for (int c = 0; c < N; ++c) {
+        const int* wd = gwin + c * kWinWords;
+        const int nb = wd[5];
+        if (nb <= 0) continue;
+        const int kind = wd[0], base = wd[1], nphi = wd[2], nw = wd[3], b0 = wd[4], iw0 = wd[6], iw1 = wd[7];
+        const float* ps = gprop + c * kSlotWords;
+        const PosState q{ps[0], ps[1], ps[2], ps[6 + ci(0, 0)], ps[6 + ci(1, 0)], ps[6 + ci(1, 1)],
+                         ps[6 + ci(2, 0)], ps[6 + ci(2, 1)], ps[6 + ci(2, 2)]};
+        const float cscore = ps[27] + 10.0f;
+        int acc = 0;
+        for (int k = 0; k < nb; ++k) {
+          int b = (b0 + k) % nphi;
+          if (b < 0) b += nphi;
+          const int beg = __ldg(&a.bin_off[base + b * nw + iw0]);
+          const int end = __ldg(&a.bin_off[base + b * nw + iw1 + 1]);
+          for (int qh = beg + li; qh < end; qh += GS) {
+            const HitRec hr = load_rec(a.rec, qh);
+            const float chi2 = hit_chi2(kind, q, hr);
+            ++n_chi2;
+            if (chi2 < cut) {
+              insert_child<NMAX>(keys, kpos, child_key(cscore - chi2, c, (uint32_t)hr.orig), qh);
+              ++acc;
             }
-            ++nk;
           }
         }
-      }
-      if (a.debug) {
-        // brute force over the whole layer: accepted hits must lie in the window
-        const int beg = __ldg(&a.bin_off[base]);
-        const int end = __ldg(&a.bin_off[base + ly.nphi * ly.nw]);
-        for (int q = beg; q < end; ++q) {
-          const HitRec hr = load_rec(a.rec, q);
-          if (hit_chi2(kind, p, C, hr) < cut) {
-            const int lb = hr.bin - ly.bin_base;
-            const int ip = lb / ly.nw, iw = lb - ip * ly.nw;
-            int d = (ip - b0) % ly.nphi;
-            if (d < 0) d += ly.nphi;
-            if (!(iw >= iw0 && iw <= iw1 && d < nb)) ++n_viol;
+        if (acc) atomicAdd(&gcnt[c], acc);
+        if (a.debug) {
+          // brute force over the whole layer: accepted hits must lie in the window
+          const int lbase = base - ebin;
+          const int beg = __ldg(&a.bin_off[base]);
+          const int end = __ldg(&a.bin_off[base + nphi * nw]);
+          for (int qh = beg + li; qh < end; qh += GS) {
+            const HitRec hr = load_rec(a.rec, qh);
+            if (hit_chi2(kind, q, hr) < cut) {
+              const int lb = hr.bin - lbase;
+              const int ip = lb / nw, iw = lb - ip * nw;
+              int d = (ip - b0) % nphi;
+              if (d < 0) d += nphi;
+              if (!(iw >= iw0 && iw <= iw1 && d < nb)) ++n_viol;
+            }
           }
         }
-      }
-      if (nholes + 1 <= a.max_holes) {
-        uint64_t kk = child_key(score - 10.0f, li, kHoleKey);
-        int kp = -1;
-#pragma unroll
-        for (int j = 0; j < NMAX; ++j) {
-          if (kk < keys[j]) {
-            uint64_t tk = keys[j];
-            keys[j] = kk;
-            kk = tk;
-            int tp = kpos[j];
-            kpos[j] = kp;
-            kp = tp;
-          }
-        }
-        ++nk;
-      }
-      if (nk > 0) {
-        // publish the propagated state for the children to clone
-#pragma unroll
-        for (int k = 0; k < 6; ++k) myslot[k] = p[k];
-#pragma unroll
-        for (int k = 0; k < 21; ++k) myslot[6 + k] = C[k];
-        myslot[30] = nrho;
-        myslot[31] = nzeta;
-        myslot[29] = __int_as_float(nholes | (nl << 16));
       }
     }
-    const bool finishing = active && (nl < 0 || nk == 0);
+    if (hole_ok) insert_child<NMAX>(keys, kpos, child_key(score - 10.0f, li, kHoleKey), -1);
     __syncwarp();
+    const int nk = nl >= 0 ? cnt[warp * 32 + lane] + (hole_ok ? 1 : 0) : 0;
+    const bool finishing = active && (nl < 0 || nk == 0);
     // ---- (4) per-seed selection: N rounds of group min over the lanes' heads
     uint64_t my_child = ~0ull;
     int my_pos = -1;
     for (int r = 0; r < N; ++r) {
       const uint64_t head = keys[0];
-      const uint64_t bestk = group_min(head, gbase, li, N);
-      const bool win = (head == bestk) && bestk != ~0ull && gvalid;
-      const unsigned wm = __ballot_sync(0xffffffffu, win) & gmask;
+      const uint64_t bestk = group_min(head, GS);
+      const bool win_ = (head == bestk) && bestk != ~0ull && gvalid;
+      const unsigned wm = __ballot_sync(0xffffffffu, win_) & gmask;
       const int wl = wm ? __ffs(wm) - 1 : lane;
       const int wpos = __shfl_sync(0xffffffffu, kpos[0], wl);
       if (li == r && wm) {
         my_child = bestk;
         my_pos = wpos;
       }
-      if (win) {
+      if (win_) {
 #pragma unroll
         for (int j = 0; j < NMAX - 1; ++j) {
           keys[j] = keys[j + 1];
@@ -420,12 +434,12 @@ __global__ void __launch_bounds__(kThreads) k_build(const BuildDev a) {
     // ---- (5) finished candidates: keep the group's best (score, then earlier step, lower slot)
     {
       const uint64_t fk = finishing ? (((uint64_t)ordered(score) << 32) | (uint32_t)(NMAX - li)) : 0ull;
-      const uint64_t fb = group_max(fk, gbase, li, N);
+      const uint64_t fb = group_max(fk, GS);
       if (finishing && fk == fb) {
         const int last = __float_as_int(best[30]);
         if (last == -2 || score > best[27]) {
 #pragma unroll
-          for (int k = 0; k < 27; ++k) best[k] = myslot[k];
+          for (int k = 0; k < 27; ++k) best[k] = mypre[k];
           best[27] = score;
           best[28] = __int_as_float(nh);
           best[29] = __int_as_float(nholes);
@@ -440,7 +454,7 @@ __global__ void __launch_bounds__(kThreads) k_build(const BuildDev a) {
     if (my_child != ~0ull) {
       const int parent = (int)((my_child >> 28) & 0xFu);
       const uint32_t hk = (uint32_t)(my_child & 0x0FFFFFFFu);
-      const float* ps = gslots + parent * kSlotWords;
+      const float* ps = gprop + parent * kSlotWords;
 #pragma unroll
       for (int k = 0; k < 6; ++k) p[k] = ps[k];
 #pragma unroll
@@ -474,7 +488,7 @@ __global__ void __launch_bounds__(kThreads) k_build(const BuildDev a) {
       const int64_t S = a.n_seeds;
       const int last = __float_as_int(best[30]);
       const int bslot = __float_as_int(best[31]);
-      for (int k = li; k < 27; k += N) {
+      for (int k = li; k < 27; k += GS) {
         if (k < 6)
           a.out_par[k * S + seed] = best[k];
         else
@@ -512,7 +526,6 @@ __global__ void __launch_bounds__(kThreads) k_build(const BuildDev a) {
     }
     __syncwarp();
     fetch(done);
-    __syncwarp();
   }
   // ---- counters
 #pragma unroll
@@ -533,27 +546,31 @@ __global__ void __launch_bounds__(kThreads) k_build(const BuildDev a) {
 }
 
 template <int NMAX>
-size_t build_smem(int L) {
-  return sizeof(GeomDev) + (size_t)kWarps * 32 * kSlotWords * 4 + (size_t)kWarps * max_groups<NMAX>() * 32 * 4 +
-         (size_t)kWarps * max_groups<NMAX>() * L * NMAX * 4;
+size_t build_smem(int L, int W, int GS) {
+  const int NG = 32 / GS;
+  return sizeof(GeomDev) + (size_t)W * 32 * (2 * kSlotWords + kWinWords + 1) * 4 + (size_t)W * NG * 32 * 4 +
+         (size_t)W * NG * L * NMAX * 4;
 }
 
 template <int NMAX>
 cudaError_t run_build(mkf_ctx* ctx, const BuildDev& d, cudaStream_t st) {
-  const size_t sm = build_smem<NMAX>(ctx->geom.n_layers);
+  int W = ctx->build_warps;
+  if (W < 1 || W > kMaxWarps) W = 4;
+  const int GS = d.gsize;
+  const size_t sm = build_smem<NMAX>(ctx->geom.n_layers, W, GS);
   cudaError_t e = cudaFuncSetAttribute(k_build<NMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build<NMAX>, kThreads, sm);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build<NMAX>, W * 32, sm);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
-  int64_t groups_needed = (d.n_seeds + (32 / d.ncand) - 1) / (32 / d.ncand);
-  int64_t blocks = (groups_needed + kWarps - 1) / kWarps;
+  const int64_t groups_needed = (d.n_seeds + (32 / GS) - 1) / (32 / GS);
+  const int64_t blocks = (groups_needed + W - 1) / W;
   int64_t grid = (int64_t)ctx->n_sm * per_sm;
   if (blocks < grid) grid = blocks;
   if (grid < 1) grid = 1;
   ctx->tick(kTBuild, st);
-  k_build<NMAX><<<(unsigned)grid, kThreads, sm, st>>>(d);
+  k_build<NMAX><<<(unsigned)grid, W * 32, sm, st>>>(d);
   ctx->tock(kTBuild, st);
   return cudaGetLastError();
 }
@@ -580,6 +597,11 @@ cudaError_t launch_build(mkf_ctx* ctx, const BuildArgs& a, cudaStream_t st) {
     d.n_events = ctx->n_events;
     d.chi2_cut = a.chi2_cut;
     d.ncand = a.max_cands;
+    {
+      int gs = 1;
+      while (gs < a.max_cands) gs <<= 1;
+      d.gsize = ctx->build_group > gs ? ctx->build_group : gs;
+    }
     d.max_holes = a.max_holes;
     d.debug = ctx->debug_window;
     d.out_hits = a.out_hits;

@@ -94,7 +94,9 @@ cudaError_t launch_fit(mkf_ctx* ctx, int direction, const float* xyz, const floa
                        int64_t n_tracks, const float* align, const float* x0, float* out_par, float* out_cov,
                        float* out_chi2, int* out_ok, float* ckpt, cudaStream_t st) {
   if (n_tracks == 0) return cudaSuccess;
-  const int T = 128;
+  // one thread per track; small blocks when there are few tracks so that the
+  // work spreads over every SM
+  const int T = n_tracks >= (int64_t)ctx->n_sm * 128 ? 128 : (n_tracks >= (int64_t)ctx->n_sm * 64 ? 64 : 32);
   const int tid = direction > 0 ? kTFit : kTBackward;
   const unsigned grid = (unsigned)((n_tracks + T - 1) / T);
   ctx->tick(tid, st);

@@ -386,7 +386,9 @@ cudaError_t launch_fit_adjoint(mkf_ctx* ctx, const float* xyz, const float* lcov
   if ((e = cudaMemsetAsync(g_x0, 0, (size_t)L * sizeof(float), st))) return e;
   if (n_tracks == 0) return cudaSuccess;
   ctx->tick(kTAdjoint, st);
-  k_fit_adjoint<<<(unsigned)((n_tracks + kAdjThreads - 1) / kAdjThreads), kAdjThreads, 0, st>>>(
+  const int T = n_tracks >= (int64_t)ctx->n_sm * kAdjThreads ? kAdjThreads
+              : (n_tracks >= (int64_t)ctx->n_sm * 64 ? 64 : 32);
+  k_fit_adjoint<<<(unsigned)((n_tracks + T - 1) / T), T, 0, st>>>(
       ctx->geom_dev.as<GeomDev>(), xyz, lcov, layer, n_hits, hits, K, n_tracks, align, x0, ckpt, g_chi2, g_par, g_cov,
       g_hit, g_align, g_x0);
   ctx->tock(kTAdjoint, st);

@@ -260,21 +260,27 @@ template <class T> struct Meas {
   T c, s, w, v00, v01, v11;
 };
 
+// Position part of a propagated state: what the chi2 of a hit needs.
+struct PosState {
+  float x, y, z;
+  float cxx, cxy, cyy, cxz, cyz, czz;
+};
+
 // Predicted chi2 (2 dof) of a hit against a propagated state; returns +inf
 // when the state is not in the hit's half plane.
-__device__ __forceinline__ float hit_chi2(int kind, const float p[6], const float C[21], const HitRec& h) {
-  if (!(fmaf(h.c, p[0], h.s * p[1]) > 0.0f)) return INFINITY;
-  float ra = fmaf(h.s, p[0], -h.c * p[1]);
+__device__ __forceinline__ float hit_chi2(int kind, const PosState& q, const HitRec& h) {
+  if (!(fmaf(h.c, q.x, h.s * q.y) > 0.0f)) return INFINITY;
+  float ra = fmaf(h.s, q.x, -h.c * q.y);
   float hab, hbb, rb;
-  float haa = fmaf(h.s * h.s, C[ci(0, 0)], fmaf(-2.0f * h.s * h.c, C[ci(1, 0)], h.c * h.c * C[ci(1, 1)]));
+  float haa = fmaf(h.s * h.s, q.cxx, fmaf(-2.0f * h.s * h.c, q.cxy, h.c * h.c * q.cyy));
   if (kind == 0) {
-    rb = h.w - p[2];
-    hab = fmaf(-h.s, C[ci(2, 0)], h.c * C[ci(2, 1)]);
-    hbb = C[ci(2, 2)];
+    rb = h.w - q.z;
+    hab = fmaf(-h.s, q.cxz, h.c * q.cyz);
+    hbb = q.czz;
   } else {
-    rb = h.w - fmaf(h.c, p[0], h.s * p[1]);
-    hab = fmaf(h.s * h.c, C[ci(1, 1)] - C[ci(0, 0)], (h.c * h.c - h.s * h.s) * C[ci(1, 0)]);
-    hbb = fmaf(h.c * h.c, C[ci(0, 0)], fmaf(2.0f * h.s * h.c, C[ci(1, 0)], h.s * h.s * C[ci(1, 1)]));
+    rb = h.w - fmaf(h.c, q.x, h.s * q.y);
+    hab = fmaf(h.s * h.c, q.cyy - q.cxx, (h.c * h.c - h.s * h.s) * q.cxy);
+    hbb = fmaf(h.c * h.c, q.cxx, fmaf(2.0f * h.s * h.c, q.cxy, h.s * h.s * q.cyy));
   }
   float Raa = haa + h.v00, Rab = hab + h.v01, Rbb = hbb + h.v11;
   float det = fmaf(Raa, Rbb, -Rab * Rab);
@@ -286,6 +292,10 @@ __device__ __forceinline__ float hit_chi2(int kind, const float p[6], const floa
   // inside the search window, which is built on the same bound.
   float chi2 = det > 0.0f ? num / det : INFINITY;
   return fmaxf(chi2, fmaxf(ra * ra / Raa, rb * rb / Rbb));
+}
+
+__device__ __forceinline__ PosState pos_state(const float p[6], const float C[21]) {
+  return PosState{p[0], p[1], p[2], C[ci(0, 0)], C[ci(1, 0)], C[ci(1, 1)], C[ci(2, 0)], C[ci(2, 1)], C[ci(2, 2)]};
 }
 
 // Kalman update with the hit: B = C H^T, R = V + H B, K = B R^-1,

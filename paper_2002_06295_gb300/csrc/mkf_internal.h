@@ -93,6 +93,8 @@ struct mkf_ctx {
   mkf::GeomDev geom{};
   mkf::DevBuf geom_dev;
   int debug_window = 0;
+  int build_warps = 4;   // warps per block of the building kernel
+  int build_group = 0;   // lanes per seed (0: max_cands rounded up to a power of two)
 
   // binning
   bool binned = false;
