@@ -28,8 +28,13 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "C2 CMS-like event: 38 surfaces (14 barrel + 24 disk), 5000 tracks, ~85k hits incl. 20% noise, " \
-           "6 candidates/seed, chi2<30, then refit (fwd + adjoint + bwd) of every found track"
+WORKLOADS = {
+    "c2": "C2 CMS-like event: 38 surfaces (14 barrel + 24 disk), 5000 tracks, ~85k hits incl. 20% noise, "
+          "6 candidates/seed, chi2<30, then refit (fwd + adjoint + bwd) of every found track",
+    "c3": "C3 batch: 256 events of the 10-cylinder barrel, 200..8000 tracks/event, 4 candidates/seed, "
+          "then refit (fwd + adjoint + bwd) of every found track",
+    "c5": "C5 batch: 64 events x 10000 tracks, 10-cylinder barrel, 50% noise, 8 candidates/seed, "
+          "then refit (fwd + adjoint + bwd) of every found track"}
 METRIC = "candidate Kalman steps/s"
 UNIT = "cand-steps/s"
 
@@ -38,7 +43,8 @@ UNIT = "cand-steps/s"
 # counts, so disk-heavy work is under-counted
 FLOPS_NAV_TEST = 44       # one surface tested by the navigation (crossing path + acceptance)
 FLOPS_CAND_STEP = 600     # helix 46 + Jacobian 84 + J C J^T 408 + material 25 + window ~35
-FLOPS_CHI2 = 40           # one candidate-hit chi2 (with the Cauchy-Schwarz floor)
+FLOPS_BOX = 7             # one candidate-hit pair examined: residuals r_a, r_b + half-plane test
+FLOPS_CHI2 = 33           # rest of the chi2 of a pair that passes the box test (with the Cauchy-Schwarz floor)
 FLOPS_UPDATE = 625        # one Kalman update of a kept child, Joseph-form covariance
 FP32_LANES = 128          # per SM (Blackwell)
 
@@ -52,6 +58,9 @@ def parse():
     ap.add_argument("--cpu-sample-seeds", type=int, default=0,
                     help="seeds per oracle sample (0: sized for ~15 s of CPU work)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the C3 batched-vs-plain and C4 fit-gradient lines")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c5"],
+                    help="timed workload (c2: the CMS-like event the metric is quoted on)")
     return ap.parse_args()
 
 
@@ -125,7 +134,7 @@ def run_reference(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": "%d seeds of the event per step" % per_step},
+            "config": {"workload": WORKLOADS["c2"], "sample": "%d seeds of the event per step" % per_step},
             "impl": "reference",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": "%d seeds x %d steps of the 5000-seed event, brute-force hit search, "
@@ -186,6 +195,127 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def measure_batched(mkf, tune, dev, reps=3):
+    """C3: 256 events of uneven size (200..8000 tracks, log-uniform) built in
+    one call (batched, persistent kernel) against 256 single-event calls of
+    the same library (plain).  Device time of binning + building + dedup."""
+    import torch
+
+    import synth
+    b = synth.make_batch(3)
+    g = b.geom
+    spec = synth.CONFIGS[3]
+    kw = dict(chi2_cut=spec["chi2_cut"], max_cands=spec["max_cands"], max_holes=spec["max_holes"],
+              min_hits=spec["min_hits"], dup_frac=spec["dup_frac"])
+    f32 = dict(dtype=torch.float32, device=dev)
+    xyz = torch.tensor(b.cat("hit_xyz").T.copy(), **f32)
+    lcov = torch.tensor(b.cat("hit_lcov").T.copy(), **f32)
+    lay = torch.tensor(b.cat("hit_layer"), dtype=torch.int32, device=dev)
+    sp = torch.tensor(b.cat("seed_par").T.copy(), **f32)
+    sc = torch.tensor(b.cat("seed_cov").T.copy(), **f32)
+    hoff = torch.tensor(b.hit_off, dtype=torch.int64, device=dev)
+    soff = torch.tensor(b.seed_off, dtype=torch.int64, device=dev)
+    ctx = mkf.Context(dev.index)
+    mkf.mkf_load_geometry(ctx, g.table(), g.bz)
+    tb = tune.autotune_build(ctx, g.table(), g.bz, xyz, lcov, lay, hoff, sp, sc, soff, max_cands=kw["max_cands"])
+    out = None
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, device=dev)
+    bt = []
+    for r in range(reps + 1):
+        flush.fill_(float(r))
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        mkf.mkf_bin_hits(ctx, xyz, lcov, lay, hoff)
+        out = mkf.mkf_build_tracks(ctx, sp, sc, soff, out=out, **kw)
+        e.record(stream)
+        e.synchronize()
+        if r:
+            bt.append(a.elapsed_time(e))
+    steps = mkf.mkf_get_stats(ctx)["cand_steps"]
+    # plain: the same library called once per event (configuration tuned on one event)
+    evs = []
+    for i, ev in enumerate(b.events):
+        evs.append(dict(xyz=torch.tensor(ev.hit_xyz.T.copy(), **f32), lcov=torch.tensor(ev.hit_lcov.T.copy(), **f32),
+                        lay=torch.tensor(ev.hit_layer, dtype=torch.int32, device=dev),
+                        hoff=torch.tensor([0, ev.n_hits], dtype=torch.int64, device=dev),
+                        sp=torch.tensor(ev.seed_par.T.copy(), **f32), sc=torch.tensor(ev.seed_cov.T.copy(), **f32),
+                        soff=torch.tensor([0, ev.n_seeds], dtype=torch.int64, device=dev)))
+    big = max(range(len(evs)), key=lambda i: b.events[i].n_seeds)
+    e0 = evs[big]
+    tp = tune.autotune_build(ctx, g.table(), g.bz, e0["xyz"], e0["lcov"], e0["lay"], e0["hoff"], e0["sp"], e0["sc"],
+                             e0["soff"], max_cands=kw["max_cands"])
+    outs = [mkf.alloc_build_outputs(ctx, b.events[i].n_seeds) for i in range(len(evs))]
+    pt = []
+    for r in range(2):
+        flush.fill_(float(r))
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for i, x in enumerate(evs):
+            mkf.mkf_bin_hits(ctx, x["xyz"], x["lcov"], x["lay"], x["hoff"])
+            mkf.mkf_build_tracks(ctx, x["sp"], x["sc"], x["soff"], out=outs[i], **kw)
+        e.record(stream)
+        e.synchronize()
+        pt.append(a.elapsed_time(e))
+    mkf.mkf_sync(ctx)
+    ctx.close()
+    E = b.n_events
+    bms, pms = min(bt), min(pt)
+    return {"workload": "C3: 256 events of the 10-cylinder barrel, 200..8000 tracks/event (log-uniform), "
+                        "%d seeds, %d hits, 4 candidates/seed" % (int(b.seed_off[-1]), int(b.hit_off[-1])),
+            "batched_ms": bms, "plain_ms": pms, "batched_events_per_s": E / (bms * 1e-3),
+            "plain_events_per_s": E / (pms * 1e-3), "batched_over_plain": pms / bms,
+            "batched_cand_steps_per_s": steps / (bms * 1e-3),
+            "tuned_batched": {k: tb[k] for k in ("n_phi", "n_w", "warps", "lanes")},
+            "tuned_plain": {k: tp[k] for k in ("n_phi", "n_w", "warps", "lanes")}}
+
+
+def measure_fit_gradient(mkf, dev, reps=3):
+    """C4: 100k tracks with fixed 14-hit assignments on the 14-cylinder barrel:
+    outward fit with per-layer checkpoints + hand-written adjoint of sum chi2."""
+    import numpy as np
+    import torch
+
+    import synth
+    g = synth.geometry_barrel14()
+    rng = np.random.default_rng(synth.config_seed(4))
+    ev = synth.simulate_event(g, 100000, rng, pt_range=(1.0, 10.0), eta_max=0.8)
+    hits = ev.true_hits[(ev.true_hits >= 0).sum(1) == 14]
+    keep = (ev.true_hits >= 0).sum(1) == 14
+    T, K = hits.shape
+    f32 = dict(dtype=torch.float32, device=dev)
+    xyz = torch.tensor(ev.hit_xyz.T.copy(), **f32)
+    lcov = torch.tensor(ev.hit_lcov.T.copy(), **f32)
+    lay = torch.tensor(ev.hit_layer, dtype=torch.int32, device=dev)
+    hd = torch.tensor(hits, dtype=torch.int32, device=dev)
+    sp = torch.tensor(ev.seed_par[keep].T.copy(), **f32)
+    sc = torch.tensor(ev.seed_cov[keep].T.copy(), **f32)
+    ctx = mkf.Context(dev.index)
+    mkf.mkf_load_geometry(ctx, g.table(), g.bz)
+    ckpt = torch.empty((K, 27, T), **f32)
+    gchi = torch.ones(T, **f32)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, device=dev)
+    fo = go = None
+    ts = []
+    for r in range(reps + 1):
+        flush.fill_(float(r))
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fo = mkf.mkf_fit_tracks(ctx, xyz, lcov, lay, hd, sp, sc, ckpt=ckpt, out=fo)
+        go = mkf.mkf_fit_tracks_adjoint(ctx, xyz, lcov, lay, hd, sp, sc, ckpt, g_chi2=gchi, out=go)
+        e.record(stream)
+        e.synchronize()
+        if r:
+            ts.append(a.elapsed_time(e))
+    mkf.mkf_sync(ctx)
+    ctx.close()
+    ms = min(ts)
+    return {"workload": "C4: %d tracks x 14 hits, barrel of 14 cylinders; outward fit with checkpoints "
+                        "(%.0f MB) + adjoint to hit xyz, alignment, thickness" % (T, K * 27 * T * 4 / 1e6),
+            "ms": ms, "fit_gradient_tracks_per_s": T / (ms * 1e-3)}
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -232,17 +362,23 @@ def main():
                          "one process per core, %.1f s wall" % (per, dt)}
 
     dev = torch.device("cuda", local)
-    ev = synth.make_config_event(2, rank)
-    g = ev.geom
+    cfg_id = {"c2": 2, "c3": 3, "c5": 5}[args.workload]
+    if cfg_id == 2:
+        evs = [synth.make_config_event(2, rank)]
+    else:
+        evs = [synth.make_config_event(cfg_id, rank * 10000 + e) for e in range(synth.CONFIGS[cfg_id]["n_events"])]
+    g = evs[0].geom
     ctx = mkf.Context(local)
     mkf.mkf_load_geometry(ctx, g.table(), g.bz, 64, 16)
-    spec = synth.CONFIGS[2]
+    spec = synth.CONFIGS[cfg_id]
     f32 = dict(dtype=torch.float32)
-    host = dict(xyz=torch.tensor(ev.hit_xyz.T.copy(), **f32), lcov=torch.tensor(ev.hit_lcov.T.copy(), **f32),
-                layer=torch.tensor(ev.hit_layer, dtype=torch.int32),
-                hoff=torch.tensor([0, ev.n_hits], dtype=torch.int64),
-                sp=torch.tensor(ev.seed_par.T.copy(), **f32), sc=torch.tensor(ev.seed_cov.T.copy(), **f32),
-                soff=torch.tensor([0, ev.n_seeds], dtype=torch.int64))
+    cat = lambda name: np.concatenate([getattr(e, name) for e in evs], 0)
+    n_hits = int(sum(e.n_hits for e in evs))
+    host = dict(xyz=torch.tensor(cat("hit_xyz").T.copy(), **f32), lcov=torch.tensor(cat("hit_lcov").T.copy(), **f32),
+                layer=torch.tensor(cat("hit_layer"), dtype=torch.int32),
+                hoff=torch.tensor(np.concatenate([[0], np.cumsum([e.n_hits for e in evs])]), dtype=torch.int64),
+                sp=torch.tensor(cat("seed_par").T.copy(), **f32), sc=torch.tensor(cat("seed_cov").T.copy(), **f32),
+                soff=torch.tensor(np.concatenate([[0], np.cumsum([e.n_seeds for e in evs])]), dtype=torch.int64))
     host = {k: v.pin_memory() for k, v in host.items()}
     d = {k: v.to(dev) for k, v in host.items()}
     # launch shape and bin granularity picked on this event (not timed)
@@ -250,7 +386,7 @@ def main():
     tuned = tune.autotune_build(ctx, g.table(), g.bz, d["xyz"], d["lcov"], d["layer"], d["hoff"], d["sp"], d["sc"],
                                 d["soff"], max_cands=spec["max_cands"], chi2_cut=spec["chi2_cut"],
                                 max_holes=spec["max_holes"], min_hits=spec["min_hits"], dup_frac=spec["dup_frac"])
-    S, L = ev.n_seeds, g.n_layers
+    S, L = int(sum(e.n_seeds for e in evs)), g.n_layers
     out = mkf.alloc_build_outputs(ctx, S)
     ckpt = torch.empty((L, 27, S), dtype=torch.float32, device=dev)
     fit_out = dict(par=torch.empty((6, S), device=dev), cov=torch.empty((21, S), device=dev),
@@ -258,7 +394,7 @@ def main():
     bwd_out = dict(par=torch.empty((6, S), device=dev), cov=torch.empty((21, S), device=dev),
                    chi2=torch.empty(S, device=dev), ok=torch.empty(S, dtype=torch.int32, device=dev))
     g_chi2 = torch.ones(S, device=dev)
-    adj_out = dict(g_hit=torch.empty((3, ev.n_hits), device=dev), g_align=torch.empty((L, 3), device=dev),
+    adj_out = dict(g_hit=torch.empty((3, n_hits), device=dev), g_align=torch.empty((L, 3), device=dev),
                    g_x0=torch.empty(L, device=dev))
     has_adjoint = [True]
     stream = torch.cuda.current_stream()
@@ -293,13 +429,13 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    tev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     build_ms, bin_ms, fit_ms, adj_ms, bwd_ms, dd_ms = [], [], [], [], [], []
     for k in range(args.steps):
         flush.fill_(float(k))
-        evs[k][0].record(stream)
+        tev[k][0].record(stream)
         step(d)
-        evs[k][1].record(stream)
+        tev[k][1].record(stream)
         tm = mkf.mkf_get_timings(ctx)
         build_ms.append(tm["build"]); bin_ms.append(tm["bin"]); fit_ms.append(tm["fit"])
         adj_ms.append(tm["adjoint"]); bwd_ms.append(tm["backward"]); dd_ms.append(tm["dedup"])
@@ -307,7 +443,7 @@ def main():
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in evs]
+    step_ms = [a.elapsed_time(b) for a, b in tev]
     total_ms = sum(step_ms)
     if dist:
         t = torch.tensor([total_ms], device=dev)
@@ -342,12 +478,18 @@ def main():
 
     if rank != 0:
         return
+    secondary = None
+    if world == 1 and not args.no_secondary:
+        from paper_2002_06295_gb300 import tune as _tune
+        secondary = {"batched_vs_plain": measure_batched(mkf, _tune, dev),
+                     "fit_gradient": measure_fit_gradient(mkf, dev)}
     units = stats["cand_steps"] * world
     value = units * args.steps / (total_ms * 1e-3)
     e2e_value = units * args.steps / (sum(e2e_ms) * 1e-3)
     b_ms = statistics.mean(build_ms)
     alg_flops = (stats["nav_tests"] * FLOPS_NAV_TEST + stats["cand_steps"] * FLOPS_CAND_STEP
-                 + stats["chi2_evals"] * FLOPS_CHI2 + stats["updates"] * FLOPS_UPDATE)
+                 + stats["chi2_evals"] * FLOPS_BOX + stats["chi2_full"] * FLOPS_CHI2
+                 + stats["updates"] * FLOPS_UPDATE)
     achieved = alg_flops / (b_ms * 1e-3) / 1e12
     props = torch.cuda.get_device_properties(dev)
     max_mhz = clk.get("sm_max_mhz") or measured_peaks().get("sm_max_mhz", 2070.0)
@@ -357,11 +499,12 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "events_per_step_per_gpu": 1, "tracks": S, "hits": ev.n_hits,
+        "config": {"workload": WORKLOADS[args.workload], "events_per_step_per_gpu": len(evs), "tracks": S,
+                   "hits": n_hits,
                    "surfaces": L, "max_cands": spec["max_cands"], "l2": "flushed (256 MB write) between timed steps",
                    "adjoint_in_step": has_adjoint[0],
                    "tuned": {k: tuned[k] for k in ("n_phi", "n_w", "warps", "lanes")}},
-        "events_per_s": world * args.steps / (total_ms * 1e-3),
+        "events_per_s": world * len(evs) * args.steps / (total_ms * 1e-3),
         "fit_tracks_per_s": world * S * args.steps / (total_ms * 1e-3),
         "stage_ms": {"bin": statistics.mean(bin_ms), "build": b_ms, "dedup": statistics.mean(dd_ms),
                      "fit": statistics.mean(fit_ms), "adjoint": statistics.mean(adj_ms) if has_adjoint[0] else None,
@@ -376,6 +519,7 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": statistics.mean(e2e_ms)},
         "gpu_launches": launches_per_step * args.steps,
+        "secondary": secondary,
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)

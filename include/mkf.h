@@ -97,6 +97,9 @@ mkf_status mkf_bin_hits(mkf_ctx* ctx, const float* xyz, const float* lcov, const
 /* Read back the binning (for inspection and tests): perm [H] original id of
  * each sorted position, bin_off [n_bins_total+1] first sorted position of each
  * (event, layer, bin), n_bins_total = n_events * sum_l(n_phi_l * n_w_l).
+ * The first call after mkf_bin_hits sorts each bin by original id (a kernel on
+ * `stream`), so the order read back is a stable sort by bin; building does not
+ * depend on the order inside a bin and does not wait for this sort.
  * DEVICE output pointers; either may be NULL.  Returns n_bins_total in *n_bins. */
 mkf_status mkf_get_binning(mkf_ctx* ctx, int* perm, int* bin_off, int64_t* n_bins, void* stream);
 
@@ -144,8 +147,10 @@ mkf_status mkf_set_build_config(mkf_ctx* ctx, int warps_per_block, int lanes_per
 mkf_status mkf_set_debug(mkf_ctx* ctx, int brute_force_window_check);
 
 /* Work counters of the last mkf_build_tracks (synchronises `stream`):
- * [0] candidate steps, [1] chi2 evaluations, [2] hit updates, [3] tracks kept,
- * [4] window violations (debug), [5] navigation surface tests, [6] seeds.
+ * [0] candidate steps, [1] candidate-hit pairs examined in the search windows
+ * (each gets the window box test), [2] hit updates, [3] tracks kept,
+ * [4] window violations (debug), [5] navigation surface tests, [6] seeds,
+ * [7] pairs that passed the box test and had their chi2 computed.
  * HOST output of n <= 8 values. */
 mkf_status mkf_get_stats(mkf_ctx* ctx, int64_t* out, int n, void* stream);
 

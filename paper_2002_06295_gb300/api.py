@@ -148,12 +148,13 @@ def mkf_set_debug(ctx, brute_force_window_check):
     ctx._check(ctx.lib.mkf_set_debug(ctx.h, int(bool(brute_force_window_check))), "mkf_set_debug")
 
 
-STAT_NAMES = ("cand_steps", "chi2_evals", "updates", "tracks_kept", "window_violations", "nav_tests", "seeds")
+STAT_NAMES = ("cand_steps", "chi2_evals", "updates", "tracks_kept", "window_violations", "nav_tests", "seeds",
+              "chi2_full")
 
 
 def mkf_get_stats(ctx, stream=None):
     buf = (ctypes.c_int64 * 8)()
-    ctx._check(ctx.lib.mkf_get_stats(ctx.h, ctypes.cast(buf, ctypes.c_void_p), 7, _stream(stream)), "mkf_get_stats")
+    ctx._check(ctx.lib.mkf_get_stats(ctx.h, ctypes.cast(buf, ctypes.c_void_p), len(STAT_NAMES), _stream(stream)), "mkf_get_stats")
     return {k: int(buf[i]) for i, k in enumerate(STAT_NAMES)}
 
 

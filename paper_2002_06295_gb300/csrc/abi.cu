@@ -153,6 +153,7 @@ mkf_status mkf_get_binning(mkf_ctx* ctx, int* perm, int* bin_off, int64_t* n_bin
   if (!ctx->binned) return ctx->fail(MKF_ERR_STATE, "hits not binned");
   cudaStream_t st = (cudaStream_t)stream;
   if (n_bins) *n_bins = ctx->n_bins_total;
+  MKF_CUDA(launch_bin_order(ctx, st), "bin order");
   if (perm && ctx->n_hits)
     MKF_CUDA(cudaMemcpyAsync(perm, ctx->perm.p, ctx->n_hits * sizeof(int), cudaMemcpyDeviceToDevice, st), "perm");
   if (bin_off)

@@ -2,9 +2,9 @@
 // no modules, the search relies on the 3-D hit positions).
 //
 // key = event * B + layer_base + phi_bin * n_w + w_bin   (w = z on a barrel, r on a disk)
-// A counting sort: per-key counts (atomics) -> exclusive scan -> scatter; the
-// order inside a bin is then made ascending in the caller's hit index, so the
-// result equals a stable sort by key.  Each sorted hit is stored as a 32-byte
+// A counting sort: per-key counts (atomics) -> exclusive scan -> scatter.  The
+// order inside a bin is made ascending in the caller's hit index only when the
+// binning is read back (the search does not depend on it).  Each sorted hit is stored as a 32-byte
 // measurement record (cos phi_h, sin phi_h, w, V) ready for the chi2 kernel.
 #include "mkf_device.cuh"
 #include "mkf_internal.h"
@@ -29,36 +29,64 @@ __device__ __forceinline__ int event_of(const int64_t* off, int n_events, int64_
   return lo;
 }
 
+// Bin key and rank of every hit, and the largest hit variances per (event,
+// layer).  The variance maxima are first reduced in shared memory over the
+// block's hits (a block's consecutive hits lie in one or two events), so the
+// global atomics per (event, layer) are one per block instead of one per hit.
 __global__ void k_bin_keys(const GeomDev* __restrict__ gdev, const float* __restrict__ xyz,
                            const float* __restrict__ lcov, const int* __restrict__ layer, int64_t n_hits,
                            const int64_t* __restrict__ ev_off, int n_events, int* __restrict__ keys,
                            int* __restrict__ ranks, int* __restrict__ counts, float* __restrict__ vmax,
                            int* __restrict__ status) {
-  const int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (h >= n_hits) return;
+  __shared__ int sv[2][MKF_MAX_LAYERS][2];   // float bits; variances are >= 0, so int order = float order
+  __shared__ int e_first;
   const int L = gdev->n_layers;
-  const int l = layer[h];
-  if (l < 0 || l >= L) {
-    keys[h] = -1;
-    atomicOr(status, kStatBadInput);
-    return;
+  for (int i = threadIdx.x; i < 2 * MKF_MAX_LAYERS * 2; i += blockDim.x) (&sv[0][0][0])[i] = 0;
+  const int64_t h0 = (int64_t)blockIdx.x * blockDim.x;
+  if (threadIdx.x == 0) e_first = event_of(ev_off, n_events, h0 < n_hits ? h0 : n_hits - 1);
+  __syncthreads();
+  const int64_t h = h0 + threadIdx.x;
+  if (h < n_hits) {
+    const int l = layer[h];
+    if (l < 0 || l >= L) {
+      keys[h] = -1;
+      atomicOr(status, kStatBadInput);
+    } else {
+      const LayerDev ly = gdev->L[l];
+      const float x = xyz[h], y = xyz[n_hits + h], z = xyz[2 * n_hits + h];
+      const float phi = atan2f(y, x);
+      const float w = ly.kind == 0 ? z : sqrtf(fmaf(x, x, y * y));
+      int ip = (int)floorf((phi + kPi) * ly.phi_scale);
+      ip = min(max(ip, 0), ly.nphi - 1);
+      int iw = (int)floorf((w - ly.lo) * ly.w_scale);
+      iw = min(max(iw, 0), ly.nw - 1);
+      int e = e_first;
+      if (e + 1 < n_events && h >= ev_off[e + 1]) {
+        ++e;
+        if (e + 1 < n_events && h >= ev_off[e + 1]) e = event_of(ev_off, n_events, h);
+      }
+      const int key = e * gdev->bins_per_event + ly.bin_base + ip * ly.nw + iw;
+      keys[h] = key;
+      ranks[h] = atomicAdd(&counts[key], 1);
+      // largest hit variances of the (event, layer): they bound the search window
+      const int va = __float_as_int(fmaxf(lcov[h], 0.0f)), vb = __float_as_int(fmaxf(lcov[n_hits + h], 0.0f));
+      const int de = e - e_first;
+      if (de < 2) {
+        atomicMax(&sv[de][l][0], va);
+        atomicMax(&sv[de][l][1], vb);
+      } else {
+        atomicMax(reinterpret_cast<int*>(&vmax[2 * (e * L + l)]), va);
+        atomicMax(reinterpret_cast<int*>(&vmax[2 * (e * L + l) + 1]), vb);
+      }
+    }
   }
-  const LayerDev ly = gdev->L[l];
-  const float x = xyz[h], y = xyz[n_hits + h], z = xyz[2 * n_hits + h];
-  const float phi = atan2f(y, x);
-  const float w = ly.kind == 0 ? z : sqrtf(fmaf(x, x, y * y));
-  int ip = (int)floorf((phi + kPi) * ly.phi_scale);
-  ip = min(max(ip, 0), ly.nphi - 1);
-  int iw = (int)floorf((w - ly.lo) * ly.w_scale);
-  iw = min(max(iw, 0), ly.nw - 1);
-  const int e = event_of(ev_off, n_events, h);
-  const int key = e * gdev->bins_per_event + ly.bin_base + ip * ly.nw + iw;
-  keys[h] = key;
-  ranks[h] = atomicAdd(&counts[key], 1);
-  // largest hit variances of the (event, layer): they bound the search window
-  const float va = lcov[h], vb = lcov[n_hits + h];
-  atomicMax(reinterpret_cast<int*>(&vmax[(2 * (e * L + l)) + 0]), __float_as_int(fmaxf(va, 0.0f)));
-  atomicMax(reinterpret_cast<int*>(&vmax[(2 * (e * L + l)) + 1]), __float_as_int(fmaxf(vb, 0.0f)));
+  __syncthreads();
+  for (int i = threadIdx.x; i < 2 * L * 2; i += blockDim.x) {
+    const int de = i / (2 * L), l = (i / 2) % L, c = i & 1;
+    const int v = sv[de][l][c];
+    if (v > 0 && e_first + de < n_events)
+      atomicMax(reinterpret_cast<int*>(&vmax[2 * ((e_first + de) * L + l) + c]), v);
+  }
 }
 
 // inclusive warp scan
@@ -145,7 +173,8 @@ __global__ void k_scan_apply(const int* __restrict__ in, int64_t n, const int* _
 __global__ void k_bin_scatter(const GeomDev* __restrict__ gdev, const float* __restrict__ xyz,
                               const float* __restrict__ lcov, const int* __restrict__ layer, int64_t n_hits,
                               const int* __restrict__ keys, const int* __restrict__ ranks,
-                              const int* __restrict__ bin_off, float4* __restrict__ rec, int* __restrict__ perm) {
+                              const int* __restrict__ bin_off, float4* __restrict__ rec,
+                              float4* __restrict__ rec_orig, int* __restrict__ perm) {
   const int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (h >= n_hits) return;
   const int key = keys[h];
@@ -157,9 +186,13 @@ __global__ void k_bin_scatter(const GeomDev* __restrict__ gdev, const float* __r
   const float ir = 1.0f / r;
   const float w = ly.kind == 0 ? z : r;
   const int local_bin = key % gdev->bins_per_event;
-  rec[2 * pos] = make_float4(x * ir, y * ir, w, lcov[h]);
-  rec[2 * pos + 1] = make_float4(lcov[2 * n_hits + h], lcov[n_hits + h], __int_as_float((int)h),
-                                 __int_as_float(local_bin));
+  const float4 r0 = make_float4(x * ir, y * ir, w, lcov[h]);
+  const float4 r1 = make_float4(lcov[2 * n_hits + h], lcov[n_hits + h], __int_as_float((int)h),
+                                __int_as_float(local_bin));
+  rec[2 * pos] = r0;
+  rec[2 * pos + 1] = r1;
+  rec_orig[2 * h] = r0;
+  rec_orig[2 * h + 1] = r1;
   perm[pos] = (int)h;
 }
 
@@ -196,6 +229,7 @@ cudaError_t launch_bin_hits(mkf_ctx* ctx, const float* xyz, const float* lcov, c
   const int64_t H = n_hits;
   cudaError_t e;
   if ((e = ctx->rec.ensure((size_t)(H > 0 ? H : 1) * 32)) != cudaSuccess) return e;
+  if ((e = ctx->rec_orig.ensure((size_t)(H > 0 ? H : 1) * 32)) != cudaSuccess) return e;
   if ((e = ctx->perm.ensure((size_t)(H > 0 ? H : 1) * 4)) != cudaSuccess) return e;
   if ((e = ctx->keys.ensure((size_t)(H > 0 ? H : 1) * 4)) != cudaSuccess) return e;
   if ((e = ctx->ranks.ensure((size_t)(H > 0 ? H : 1) * 4)) != cudaSuccess) return e;
@@ -227,11 +261,26 @@ cudaError_t launch_bin_hits(mkf_ctx* ctx, const float* xyz, const float* lcov, c
   if (H > 0) {
     k_bin_scatter<<<(unsigned)((H + T - 1) / T), T, 0, st>>>(gd, xyz, lcov, layer, H, ctx->keys.as<int>(),
                                                             ctx->ranks.as<int>(), ctx->bin_off.as<int>(),
-                                                            ctx->rec.as<float4>(), ctx->perm.as<int>());
-    k_bin_order<<<(unsigned)((n_bins + T - 1) / T), T, 0, st>>>(ctx->bin_off.as<int>(), n_bins,
-                                                               ctx->rec.as<float4>(), ctx->perm.as<int>());
+                                                            ctx->rec.as<float4>(), ctx->rec_orig.as<float4>(),
+                                                            ctx->perm.as<int>());
   }
+  ctx->bins_ordered = H == 0;
   ctx->tock(kTBin, st);
+  return cudaGetLastError();
+}
+
+// The building kernel does not depend on the order of the hits inside a bin
+// (candidate ranking breaks ties by the caller's hit index), so the binning
+// leaves it as the count atomics made it; mkf_get_binning sorts each bin by
+// the caller's hit index first, which makes the result a stable sort.
+cudaError_t launch_bin_order(mkf_ctx* ctx, cudaStream_t st) {
+  if (ctx->bins_ordered) return cudaSuccess;
+  const int64_t n_bins = ctx->n_bins_total;
+  const int T = 256;
+  if (n_bins > 0)
+    k_bin_order<<<(unsigned)((n_bins + T - 1) / T), T, 0, st>>>(ctx->bin_off.as<int>(), n_bins, ctx->rec.as<float4>(),
+                                                               ctx->perm.as<int>());
+  ctx->bins_ordered = true;
   return cudaGetLastError();
 }
 

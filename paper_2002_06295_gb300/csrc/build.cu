@@ -34,18 +34,18 @@ namespace mkf {
 namespace {
 
 constexpr int kMaxWarps = 8;
-constexpr int kSlotWords = 32;             // per-lane shared slot: p[6], C[21], score, nh, nholes|layer, rho, zeta
-constexpr int kWinWords = 8;               // per-lane window: kind, base bin, nphi, nw, b0, nb, iw0, iw1
+// per-lane shared slot: p[6], C[21], score, nh, nholes|layer, rho, zeta (+1 pad: an odd stride puts
+// the same word of different lanes in different banks)
+constexpr int kSlotWords = 33;
+// per-lane window: kind, base bin, nphi, nw, b0, nb, iw0, iw1, ha, hb, hit base (+2 pad, odd stride)
+constexpr int kWinWords = 13;
 constexpr uint32_t kHoleKey = 0x0FFFFFFFu;
 constexpr uint32_t kHistHole = 0x3FFFFFu;  // 22-bit local hit index field
-
-// most groups a warp can hold for a given compile-time bound NMAX on max_cands
-// (N is in (NMAX/2, NMAX] for NMAX >= 2)
-template <int NMAX> constexpr int max_groups() { return NMAX == 1 ? 32 : 32 / (NMAX / 2 + 1); }
 
 struct BuildDev {
   const GeomDev* geom;
   const float4* rec;
+  const float4* rec_orig;
   const int* bin_off;
   const float* vmax;
   const int64_t* ev_hit_off;
@@ -79,9 +79,64 @@ __device__ __forceinline__ uint32_t ordered(float f) {
 __device__ __forceinline__ float unordered(uint32_t o) {
   return __uint_as_float((o & 0x80000000u) ? (o & 0x7FFFFFFFu) : ~o);
 }
-// smaller key = better child: score descending, parent slot, hit id, hole last
+// smaller key = better child: score descending, parent slot, hit (the caller's
+// index of the hit relative to the event's first hit; kHoleKey for a hole)
 __device__ __forceinline__ uint64_t child_key(float score, int slot, uint32_t hitkey) {
   return ((uint64_t)(~ordered(score)) << 32) | ((uint64_t)slot << 28) | hitkey;
+}
+
+// Insert key k into the ascending array ts[0..n) that holds the n smallest
+// keys inserted so far (~0 = empty).  Any number of lanes may insert
+// concurrently: every key reaching slot j leaves the smaller of it and the
+// slot's value there and carries the larger on, so slot j ends up holding the
+// j-th smallest key whatever the interleaving.  Slot values only decrease, so
+// a key not below the current last slot can never enter and is dropped at once.
+__device__ __forceinline__ void top_insert(unsigned long long* ts, int n, unsigned long long k) {
+  if (!(k < *reinterpret_cast<volatile unsigned long long*>(&ts[n - 1]))) return;
+  for (int j = 0; j < n; ++j) {
+    const unsigned long long old = atomicMin(&ts[j], k);
+    if (old == ~0ull) return;
+    k = old > k ? old : k;
+  }
+}
+
+// C' = J C J^T (+ multiple scattering on C'_phiphi, C'_thetatheta) written to
+// dst[21] without touching C: the candidate keeps its pre-step state in
+// registers, which is the state a candidate that finishes here is stored with.
+// The position block of C' (xx, yx, yy, zz) is also returned for the window.
+__device__ __forceinline__ void transport_cov_into(const Jac4<float>& J, const float C[21], float ms_phi,
+                                                   float ms_theta, float* dst, float cpos[4]) {
+  constexpr int R[4] = {0, 1, 2, 4};
+  float T4[4][6];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) acc = fmaf(J.r[i][k], C[ci(k, j)], acc);
+      T4[i][j] = acc;
+    }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    dst[ci(3, R[i])] = T4[i][3];
+    dst[ci(5, R[i])] = T4[i][5];
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) acc = fmaf(T4[i][k], J.r[j][k], acc);
+      if (i == 3 && j == 3) acc += ms_phi;
+      dst[ci(R[i], R[j])] = acc;
+      if (i == 0 && j == 0) cpos[0] = acc;
+      if (i == 1 && j == 0) cpos[1] = acc;
+      if (i == 1 && j == 1) cpos[2] = acc;
+      if (i == 2 && j == 2) cpos[3] = acc;
+    }
+  }
+  dst[ci(3, 3)] = C[ci(3, 3)];
+  dst[ci(5, 3)] = C[ci(5, 3)];
+  dst[ci(5, 5)] = C[ci(5, 5)] + ms_theta;
 }
 
 __device__ __forceinline__ HitRec load_rec(const float4* __restrict__ rec, int pos) {
@@ -111,37 +166,17 @@ __device__ __forceinline__ int event_of(const int64_t* off, int n_events, int64_
   return lo;
 }
 
-// min / max over the GS lanes of a group (GS a power of two, groups aligned)
-__device__ __forceinline__ uint64_t group_min(uint64_t v, int GS) {
-  for (int off = 1; off < GS; off <<= 1) {
-    const uint64_t o = __shfl_xor_sync(0xffffffffu, v, off);
-    v = o < v ? o : v;
-  }
-  return v;
-}
-__device__ __forceinline__ uint64_t group_max(uint64_t v, int GS) {
-  for (int off = 1; off < GS; off <<= 1) {
-    const uint64_t o = __shfl_xor_sync(0xffffffffu, v, off);
-    v = o > v ? o : v;
-  }
-  return v;
+// max of a 64-bit key over the lanes of a group (gm = the group's lane mask):
+// a 32-bit reduction of the high words, then of the low words of the lanes
+// that hold the largest high word
+__device__ __forceinline__ uint64_t group_max(uint64_t v, unsigned gm) {
+  const unsigned hi = (unsigned)(v >> 32), lo = (unsigned)v;
+  const unsigned mh = __reduce_max_sync(gm, hi);
+  const unsigned ml = __reduce_max_sync(gm, hi == mh ? lo : 0u);
+  return ((uint64_t)mh << 32) | ml;
 }
 
-template <int NMAX> __device__ __forceinline__ void insert_child(uint64_t keys[NMAX], int kpos[NMAX], uint64_t kk, int kp) {
-#pragma unroll
-  for (int j = 0; j < NMAX; ++j) {
-    if (kk < keys[j]) {
-      const uint64_t tk = keys[j];
-      keys[j] = kk;
-      kk = tk;
-      const int tp = kpos[j];
-      kpos[j] = kp;
-      kp = tp;
-    }
-  }
-}
-
-template <int NMAX>
+template <int NMAX, bool DEBUG>
 __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
   extern __shared__ __align__(16) unsigned char smem[];
   GeomDev& G = *reinterpret_cast<GeomDev*>(smem);
@@ -160,29 +195,36 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
   const int warp = threadIdx.x >> 5;
   const int gi = lane / GS;
   const int li = lane - gi * GS;
-  const bool gvalid = true;
   const int gbase = gi * GS;
-  const unsigned gmask = (GS == 32 ? 0xffffffffu : ((1u << GS) - 1u)) << gbase;
+  const unsigned gfull = GS == 32 ? 0xffffffffu : ((1u << GS) - 1u);
+  const unsigned gmask = gfull << gbase;
 
-  const int NGM = NG;
-  float* pre = reinterpret_cast<float*>(smem + sizeof(GeomDev));                   // [W][32][kSlotWords]
-  float* prop = pre + W * 32 * kSlotWords;                                          // [W][32][kSlotWords]
+  float* prop = reinterpret_cast<float*>(smem + sizeof(GeomDev));                  // [W][32][kSlotWords]
   int* win = reinterpret_cast<int*>(prop + W * 32 * kSlotWords);                   // [W][32][kWinWords]
   int* cnt = win + W * 32 * kWinWords;                                              // [W][32]
-  float* bests = reinterpret_cast<float*>(cnt + W * 32);                            // [W][NGM][32]
-  uint32_t* hist = reinterpret_cast<uint32_t*>(bests + W * NGM * 32);               // [W][NGM][L][NMAX]
-  float* mypre = pre + (warp * 32 + lane) * kSlotWords;
+  int* rowp = cnt + W * 32;                                                         // [W][32]
+  int* rpre = rowp + W * 32;                                                        // [W][32]
+  int2* rbc = reinterpret_cast<int2*>(rpre + W * 32);                               // [W][32]
+  unsigned long long* top = reinterpret_cast<unsigned long long*>(rbc + W * 32);    // [W][NG][NMAX]
+  float* bests = reinterpret_cast<float*>(top + W * NG * NMAX);                     // [W][NG][32]
+  uint32_t* hist = reinterpret_cast<uint32_t*>(bests + W * NG * 32);                // [W][NG][L][NMAX]
   float* myprop = prop + (warp * 32 + lane) * kSlotWords;
   float* gprop = prop + (warp * 32 + gbase) * kSlotWords;
   int* mywin = win + (warp * 32 + lane) * kWinWords;
   int* gwin = win + (warp * 32 + gbase) * kWinWords;
-  int* gcnt = cnt + warp * 32 + gbase;
-  float* best = bests + (warp * NGM + (gvalid ? gi : 0)) * 32;
-  uint32_t* ghist = hist + (size_t)(warp * NGM + (gvalid ? gi : 0)) * L * NMAX;
+  const int* wrowp = rowp + warp * 32;
+  const int* wpre = rpre + warp * 32;
+  const int2* wbc = rbc + warp * 32;
+  const int* wwin = win + warp * 32 * kWinWords;
+  const float* wprop = prop + warp * 32 * kSlotWords;
+  float* best = bests + (warp * NG + gi) * 32;
+  unsigned long long* wtop = top + warp * NG * NMAX;
+  unsigned long long* gtop = wtop + gi * NMAX;
+  uint32_t* ghist = hist + (size_t)(warp * NG + gi) * L * NMAX;
 
   const float cut = a.chi2_cut;
   const float ck = G.c_kappa;
-  unsigned long long n_steps = 0, n_chi2 = 0, n_upd = 0, n_nav = 0, n_viol = 0;
+  unsigned long long n_steps = 0, n_chi2 = 0, n_full = 0, n_upd = 0, n_nav = 0, n_viol = 0;
 
   // per-group seed state (replicated over the group's lanes)
   int64_t seed = -1;
@@ -198,10 +240,10 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
   // of the warp together (it shuffles).
   auto fetch = [&](bool want) {
     unsigned long long s = 0;
-    if (want && gvalid && li == 0) s = atomicAdd(a.seed_ctr, 1ull);
+    if (want && li == 0) s = atomicAdd(a.seed_ctr, 1ull);
     s = __shfl_sync(0xffffffffu, s, gbase);
     if (!want) return;
-    seed = (gvalid && (int64_t)s < a.n_seeds) ? (int64_t)s : -1;
+    seed = (int64_t)s < a.n_seeds ? (int64_t)s : -1;
     active = false;
     step = 0;
     if (seed >= 0) {
@@ -224,20 +266,10 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
       }
     }
   };
-  fetch(gvalid);
+  fetch(true);
 
   for (;;) {
     if (__all_sync(0xffffffffu, seed < 0)) break;
-    // ---- (0) save the pre-step state: finished candidates are read back from here
-    if (active) {
-#pragma unroll
-      for (int k = 0; k < 6; ++k) mypre[k] = p[k];
-#pragma unroll
-      for (int k = 0; k < 21; ++k) mypre[6 + k] = C[k];
-      mypre[27] = score;
-      mypre[28] = __int_as_float(nh);
-      mypre[29] = __int_as_float(nholes);
-    }
     // ---- (1) navigation: next reachable surface outward
     int nl = -1;
     float ns = INFINITY;
@@ -273,13 +305,14 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
           const int l = ord[i];
           const LayerDev& ly = G.L[l];
           if (!(fabsf(ly.pos) > zeta + kNavEps)) continue;
-          if (!exit_known) {
-            s_lim = fminf(ns, cylinder_path(p[0], p[1], cph, sph, omega, G.r_max, +1));
-            exit_known = true;
-          }
           ++n_nav;
           const float s = plane_path(p[2], cot_t, ly.pos, +1);
           if (!(s < s_lim)) break;     // |z| ordered: later disks are farther
+          if (!exit_known) {
+            s_lim = fminf(ns, cylinder_path(p[0], p[1], cph, sph, omega, G.r_max, +1));
+            exit_known = true;
+            if (!(s < s_lim)) break;
+          }
           const auto h = helix_at(p[0], p[1], p[2], p[4], cot_t, omega, s);
           const float r = sqrtf(fmaf(h.x, h.x, h.y * h.y));
           if (r >= ly.lo && r <= ly.hi) {
@@ -300,22 +333,23 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
       const int kind = ly.kind;
       const auto h = helix_at(p[0], p[1], p[2], p[4], cot_t, omega, ns);
       const auto J = transport_jacobian(kind, p, h, ns, omega, ck, cot_t, sin_t);
-      similarity(J, C);
-      p[0] = h.x;
-      p[1] = h.y;
-      p[2] = h.z;
-      p[4] = wrap_phi(h.phi);
-      add_material(kind, ly.x0, h.x, h.y, h.cphi, h.sphi, p[3], sin_t, cos_t, C);
+      float ms_phi = 0.0f, ms_theta = 0.0f;
+      if (ly.x0 > 0.0f) {
+        ms_theta = highland_theta0_sq(kind, ly.x0, h.x, h.y, h.cphi, h.sphi, p[3], sin_t, cos_t);
+        ms_phi = ms_theta / (sin_t * sin_t);
+      }
+      float cpos[4];
+      transport_cov_into(J, C, ms_phi, ms_theta, myprop + 6, cpos);
       const float rc = sqrtf(fmaf(h.x, h.x, h.y * h.y));
       // conservative window: |r_i| < sqrt(cut R_ii) (Cauchy-Schwarz), R_ii bounded
       // by the largest eigenvalue of C_xy (or C_zz) plus the layer's largest hit variance
       const float va = __ldg(&a.vmax[2 * (ev * L + nl)]);
       const float vb = __ldg(&a.vmax[2 * (ev * L + nl) + 1]);
-      const float cxx = C[ci(0, 0)], cyy = C[ci(1, 1)], cxy = C[ci(1, 0)];
+      const float cxx = cpos[0], cyy = cpos[2], cxy = cpos[1];
       const float hd = 0.5f * (cxx - cyy);
       const float lam = 0.5f * (cxx + cyy) + sqrtf(fmaf(hd, hd, cxy * cxy));
       const float ha = sqrtf(cut * (lam + va)) * 1.05f + 1e-4f;
-      const float hb = sqrtf(cut * ((kind == 0 ? C[ci(2, 2)] : lam) + vb)) * 1.05f + 1e-4f;
+      const float hb = sqrtf(cut * ((kind == 0 ? cpos[3] : lam) + vb)) * 1.05f + 1e-4f;
       const float phic = atan2f(h.y, h.x);
       float dphi = ha >= rc ? 0.5f * kPi : asinf(ha / rc);
       dphi = dphi * 1.001f + 1e-5f;
@@ -337,10 +371,15 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
       mywin[5] = max(min((int)(hi_f - lo_f) + 1, ly.nphi), 1);
       mywin[6] = min(max((int)floorf((wlo - ly.lo) * ly.w_scale), 0), ly.nw - 1);
       mywin[7] = min(max((int)floorf((whi - ly.lo) * ly.w_scale), 0), ly.nw - 1);
-#pragma unroll
-      for (int k = 0; k < 6; ++k) myprop[k] = p[k];
-#pragma unroll
-      for (int k = 0; k < 21; ++k) myprop[6 + k] = C[k];
+      mywin[8] = __float_as_int(ha);
+      mywin[9] = __float_as_int(hb);
+      mywin[10] = hit_base;
+      myprop[0] = h.x;
+      myprop[1] = h.y;
+      myprop[2] = h.z;
+      myprop[3] = p[3];
+      myprop[4] = wrap_phi(h.phi);
+      myprop[5] = p[5];
       myprop[27] = score;
       myprop[28] = __int_as_float(nh);
       myprop[29] = __int_as_float(nholes | (nl << 16));
@@ -350,15 +389,86 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
     }
     cnt[warp * 32 + lane] = 0;
     __syncwarp();
-    // ---- (3) the group scans each candidate's window together
-    uint64_t keys[NMAX];
-    int kpos[NMAX];
+    // ---- (3) the warp scans the windows of all its candidates together.
+    // A window is nb phi rows, each a contiguous range of hits (w bins
+    // iw0..iw1).  The rows of all the warp's candidates are dealt to the 32
+    // lanes, then the hits of those rows, so every lane's loads are
+    // independent and a seed with a wide window
+    // does not hold up the warp.  Each hit gets the box test, then its chi2 if
+    // it passes; an accepted child goes straight into its seed's top-N slots.
+    if (li < N) gtop[li] = ~0ull;
+    __syncwarp();
+    {
+      const int nbl = mywin[5];
+      int incl = nbl;
 #pragma unroll
-    for (int k = 0; k < NMAX; ++k) {
-      keys[k] = ~0ull;
-      kpos[k] = -1;
+      for (int off = 1; off < 32; off <<= 1) {
+        const int o = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += o;
+      }
+      const int Mw = __shfl_sync(0xffffffffu, incl, 31);
+      rowp[warp * 32 + lane] = incl - nbl;
+      __syncwarp();
+      for (int r0 = 0; r0 < Mw; r0 += 32) {
+        const int t = r0 + lane;
+        int beg = 0, len = 0, cl = 0;
+        if (t < Mw) {
+          // candidate lane owning row t: last lane whose row prefix is <= t
+#pragma unroll
+          for (int st = 16; st > 0; st >>= 1)
+            if (wrowp[cl + st] <= t) cl += st;
+          const int* wd = wwin + cl * kWinWords;
+          int b = (wd[4] + (t - wrowp[cl])) % wd[2];
+          if (b < 0) b += wd[2];
+          const int row = wd[1] + b * wd[3];
+          beg = __ldg(&a.bin_off[row + wd[6]]);
+          len = __ldg(&a.bin_off[row + wd[7] + 1]) - beg;
+        }
+        int hin = len;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          const int o = __shfl_up_sync(0xffffffffu, hin, off);
+          if (lane >= off) hin += o;
+        }
+        const int Hw = __shfl_sync(0xffffffffu, hin, 31);
+        rpre[warp * 32 + lane] = hin - len;
+        rbc[warp * 32 + lane] = make_int2(beg, cl);
+        __syncwarp();
+        for (int h0 = 0; h0 < Hw; h0 += 32) {
+          const int h = h0 + lane;
+          if (h < Hw) {
+            // the row holding flattened hit h: last lane whose hit prefix is <= h
+            int j = 0;
+#pragma unroll
+            for (int st = 16; st > 0; st >>= 1)
+              if (wpre[j + st] <= h) j += st;
+            const int2 bc = wbc[j];
+            const int cc = bc.y;
+            const HitRec hr = load_rec(a.rec, bc.x + (h - wpre[j]));
+            const int* wd = wwin + cc * kWinWords;
+            const float* ps = wprop + cc * kSlotWords;
+            const int kind = wd[0];
+            ++n_chi2;
+            if (hit_in_box(kind, ps[0], ps[1], ps[2], hr, __int_as_float(wd[8]), __int_as_float(wd[9]))) {
+              ++n_full;
+              const PosState q{ps[0], ps[1], ps[2], ps[6 + ci(0, 0)], ps[6 + ci(1, 0)], ps[6 + ci(1, 1)],
+                               ps[6 + ci(2, 0)], ps[6 + ci(2, 1)], ps[6 + ci(2, 2)]};
+              const float chi2 = hit_chi2(kind, q, hr, cut);
+              if (chi2 < cut) {
+                atomicAdd(&cnt[warp * 32 + cc], 1);
+                const uint32_t hloc = (uint32_t)(hr.orig - wd[10]);
+                top_insert(wtop + (cc / GS) * NMAX, N,
+                           child_key(ps[27] + 10.0f - chi2, cc & (GS - 1), hloc < kHoleKey ? hloc : kHoleKey - 1));
+              }
+            }
+          }
+        }
+        __syncwarp();
+      }
     }
-    if (gvalid) {
+    if (DEBUG) {
+      // brute force over each candidate's whole layer: every accepted hit must
+      // pass the box test and lie in the window's bins
       for (int c = 0; c < N; ++c) {
         const int* wd = gwin + c * kWinWords;
         const int nb = wd[5];
@@ -367,79 +477,40 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
         const float* ps = gprop + c * kSlotWords;
         const PosState q{ps[0], ps[1], ps[2], ps[6 + ci(0, 0)], ps[6 + ci(1, 0)], ps[6 + ci(1, 1)],
                          ps[6 + ci(2, 0)], ps[6 + ci(2, 1)], ps[6 + ci(2, 2)]};
-        const float cscore = ps[27] + 10.0f;
-        int acc = 0;
-        for (int k = 0; k < nb; ++k) {
-          int b = (b0 + k) % nphi;
-          if (b < 0) b += nphi;
-          const int beg = __ldg(&a.bin_off[base + b * nw + iw0]);
-          const int end = __ldg(&a.bin_off[base + b * nw + iw1 + 1]);
-          for (int qh = beg + li; qh < end; qh += GS) {
-            const HitRec hr = load_rec(a.rec, qh);
-            const float chi2 = hit_chi2(kind, q, hr);
-            ++n_chi2;
-            if (chi2 < cut) {
-              insert_child<NMAX>(keys, kpos, child_key(cscore - chi2, c, (uint32_t)hr.orig), qh);
-              ++acc;
-            }
-          }
-        }
-        if (acc) atomicAdd(&gcnt[c], acc);
-        if (a.debug) {
-          // brute force over the whole layer: accepted hits must lie in the window
-          const int lbase = base - ebin;
-          const int beg = __ldg(&a.bin_off[base]);
-          const int end = __ldg(&a.bin_off[base + nphi * nw]);
-          for (int qh = beg + li; qh < end; qh += GS) {
-            const HitRec hr = load_rec(a.rec, qh);
-            if (hit_chi2(kind, q, hr) < cut) {
-              const int lb = hr.bin - lbase;
-              const int ip = lb / nw, iw = lb - ip * nw;
-              int d = (ip - b0) % nphi;
-              if (d < 0) d += nphi;
-              if (!(iw >= iw0 && iw <= iw1 && d < nb)) ++n_viol;
-            }
+        const int lbase = base - ebin;
+        const int beg = __ldg(&a.bin_off[base]);
+        const int end = __ldg(&a.bin_off[base + nphi * nw]);
+        for (int qh = beg + li; qh < end; qh += GS) {
+          const HitRec hr = load_rec(a.rec, qh);
+          if (hit_chi2(kind, q, hr, cut) < cut) {
+            const int lb = hr.bin - lbase;
+            const int ip = lb / nw, iw = lb - ip * nw;
+            int d = (ip - b0) % nphi;
+            if (d < 0) d += nphi;
+            const bool in_box = hit_in_box(kind, q.x, q.y, q.z, hr, __int_as_float(wd[8]), __int_as_float(wd[9]));
+            if (!(iw >= iw0 && iw <= iw1 && d < nb && in_box)) ++n_viol;
           }
         }
       }
     }
-    if (hole_ok) insert_child<NMAX>(keys, kpos, child_key(score - 10.0f, li, kHoleKey), -1);
+    if (hole_ok) top_insert(gtop, N, child_key(score - 10.0f, li, kHoleKey));
     __syncwarp();
     const int nk = nl >= 0 ? cnt[warp * 32 + lane] + (hole_ok ? 1 : 0) : 0;
     const bool finishing = active && (nl < 0 || nk == 0);
-    // ---- (4) per-seed selection: N rounds of group min over the lanes' heads
-    uint64_t my_child = ~0ull;
-    int my_pos = -1;
-    for (int r = 0; r < N; ++r) {
-      const uint64_t head = keys[0];
-      const uint64_t bestk = group_min(head, GS);
-      const bool win_ = (head == bestk) && bestk != ~0ull && gvalid;
-      const unsigned wm = __ballot_sync(0xffffffffu, win_) & gmask;
-      const int wl = wm ? __ffs(wm) - 1 : lane;
-      const int wpos = __shfl_sync(0xffffffffu, kpos[0], wl);
-      if (li == r && wm) {
-        my_child = bestk;
-        my_pos = wpos;
-      }
-      if (win_) {
-#pragma unroll
-        for (int j = 0; j < NMAX - 1; ++j) {
-          keys[j] = keys[j + 1];
-          kpos[j] = kpos[j + 1];
-        }
-        keys[NMAX - 1] = ~0ull;
-        kpos[NMAX - 1] = -1;
-      }
-    }
+    // ---- (4) per-seed selection: the slots hold the seed's best N children in
+    // order; lane li of the group takes the li-th
+    const uint64_t my_child = li < N ? gtop[li] : ~0ull;
     // ---- (5) finished candidates: keep the group's best (score, then earlier step, lower slot)
     {
       const uint64_t fk = finishing ? (((uint64_t)ordered(score) << 32) | (uint32_t)(NMAX - li)) : 0ull;
-      const uint64_t fb = group_max(fk, GS);
+      const uint64_t fb = group_max(fk, gmask);
       if (finishing && fk == fb) {
         const int last = __float_as_int(best[30]);
         if (last == -2 || score > best[27]) {
 #pragma unroll
-          for (int k = 0; k < 27; ++k) best[k] = mypre[k];
+          for (int k = 0; k < 6; ++k) best[k] = p[k];
+#pragma unroll
+          for (int k = 0; k < 21; ++k) best[6 + k] = C[k];
           best[27] = score;
           best[28] = __int_as_float(nh);
           best[29] = __int_as_float(nholes);
@@ -468,11 +539,11 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
       score = unordered(~(uint32_t)(my_child >> 32));
       uint32_t hloc = kHistHole;
       if (hk != kHoleKey) {
-        const HitRec hr = load_rec(a.rec, my_pos);
+        const HitRec hr = load_rec(a.rec_orig, hit_base + (int)hk);
         kf_update(G.L[lay].kind, p, C, hr);
         ++nh;
         ++n_upd;
-        hloc = (uint32_t)(my_pos - hit_base);
+        hloc = hk;
         if (hloc >= kHistHole) atomicOr(a.status, kStatCapacity);
       } else {
         ++nholes;
@@ -516,7 +587,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
         for (int k = last; k >= 0; --k) {
           const uint32_t e = ghist[k * NMAX + slot];
           const uint32_t hl = e & kHistHole;
-          oh[k] = hl == kHistHole ? -1 : load_rec(a.rec, hit_base + (int)hl).orig;
+          oh[k] = hl == kHistHole ? -1 : hit_base + (int)hl;
           if (ol) ol[k] = (int)((e >> 22) & 0x3Fu);
           slot = (int)(e >> 28);
         }
@@ -532,6 +603,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
   for (int o = 16; o > 0; o >>= 1) {
     n_steps += __shfl_xor_sync(0xffffffffu, n_steps, o);
     n_chi2 += __shfl_xor_sync(0xffffffffu, n_chi2, o);
+    n_full += __shfl_xor_sync(0xffffffffu, n_full, o);
     n_upd += __shfl_xor_sync(0xffffffffu, n_upd, o);
     n_nav += __shfl_xor_sync(0xffffffffu, n_nav, o);
     n_viol += __shfl_xor_sync(0xffffffffu, n_viol, o);
@@ -542,26 +614,28 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
     atomicAdd(&a.stats[2], n_upd);
     atomicAdd(&a.stats[4], n_viol);
     atomicAdd(&a.stats[5], n_nav);
+    atomicAdd(&a.stats[7], n_full);
   }
 }
 
 template <int NMAX>
 size_t build_smem(int L, int W, int GS) {
   const int NG = 32 / GS;
-  return sizeof(GeomDev) + (size_t)W * 32 * (2 * kSlotWords + kWinWords + 1) * 4 + (size_t)W * NG * 32 * 4 +
+  return sizeof(GeomDev) + (size_t)W * 32 * (kSlotWords + kWinWords + 1 + 4) * 4 + (size_t)W * NG * NMAX * 8 +
+         (size_t)W * NG * 32 * 4 +
          (size_t)W * NG * L * NMAX * 4;
 }
 
-template <int NMAX>
+template <int NMAX, bool DEBUG>
 cudaError_t run_build(mkf_ctx* ctx, const BuildDev& d, cudaStream_t st) {
   int W = ctx->build_warps;
   if (W < 1 || W > kMaxWarps) W = 4;
   const int GS = d.gsize;
   const size_t sm = build_smem<NMAX>(ctx->geom.n_layers, W, GS);
-  cudaError_t e = cudaFuncSetAttribute(k_build<NMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = cudaFuncSetAttribute(k_build<NMAX, DEBUG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build<NMAX>, W * 32, sm);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build<NMAX, DEBUG>, W * 32, sm);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   const int64_t groups_needed = (d.n_seeds + (32 / GS) - 1) / (32 / GS);
@@ -570,7 +644,7 @@ cudaError_t run_build(mkf_ctx* ctx, const BuildDev& d, cudaStream_t st) {
   if (blocks < grid) grid = blocks;
   if (grid < 1) grid = 1;
   ctx->tick(kTBuild, st);
-  k_build<NMAX><<<(unsigned)grid, W * 32, sm, st>>>(d);
+  k_build<NMAX, DEBUG><<<(unsigned)grid, W * 32, sm, st>>>(d);
   ctx->tock(kTBuild, st);
   return cudaGetLastError();
 }
@@ -587,6 +661,7 @@ cudaError_t launch_build(mkf_ctx* ctx, const BuildArgs& a, cudaStream_t st) {
     BuildDev d;
     d.geom = ctx->geom_dev.as<GeomDev>();
     d.rec = ctx->rec.as<float4>();
+    d.rec_orig = ctx->rec_orig.as<float4>();
     d.bin_off = ctx->bin_off.as<int>();
     d.vmax = ctx->vmax.as<float>();
     d.ev_hit_off = ctx->ev_hit_off.as<int64_t>();
@@ -615,14 +690,18 @@ cudaError_t launch_build(mkf_ctx* ctx, const BuildArgs& a, cudaStream_t st) {
     d.seed_ctr = ctx->seed_ctr.as<unsigned long long>();
     d.stats = ctx->stats.as<unsigned long long>();
     d.status = ctx->status.as<int>();
-    if (a.max_cands <= 1)
-      e = run_build<1>(ctx, d, st);
+    // the brute-force window check has a kernel of its own (any N <= 8), so
+    // the production kernels carry none of its code
+    if (d.debug)
+      e = run_build<8, true>(ctx, d, st);
+    else if (a.max_cands <= 1)
+      e = run_build<1, false>(ctx, d, st);
     else if (a.max_cands <= 2)
-      e = run_build<2>(ctx, d, st);
+      e = run_build<2, false>(ctx, d, st);
     else if (a.max_cands <= 4)
-      e = run_build<4>(ctx, d, st);
+      e = run_build<4, false>(ctx, d, st);
     else
-      e = run_build<8>(ctx, d, st);
+      e = run_build<8, false>(ctx, d, st);
     if (e != cudaSuccess) return e;
   }
   return launch_dedup(ctx, a.out_hits, ctx->geom.n_layers, a.out_score, ctx->track_hits.as<int>(), a.ev_seed_off,

@@ -267,8 +267,10 @@ struct PosState {
 };
 
 // Predicted chi2 (2 dof) of a hit against a propagated state; returns +inf
-// when the state is not in the hit's half plane.
-__device__ __forceinline__ float hit_chi2(int kind, const PosState& q, const HitRec& h) {
+// when the state is not in the hit's half plane.  Values at or above `cut`
+// are only guaranteed to be >= cut (the bound below is applied to the values
+// that would be accepted).
+__device__ __forceinline__ float hit_chi2(int kind, const PosState& q, const HitRec& h, float cut) {
   if (!(fmaf(h.c, q.x, h.s * q.y) > 0.0f)) return INFINITY;
   float ra = fmaf(h.s, q.x, -h.c * q.y);
   float hab, hbb, rb;
@@ -291,7 +293,21 @@ __device__ __forceinline__ float hit_chi2(int kind, const PosState& q, const Hit
   // frame), the bound is the trustworthy value.  It keeps every accepted hit
   // inside the search window, which is built on the same bound.
   float chi2 = det > 0.0f ? num / det : INFINITY;
-  return fmaxf(chi2, fmaxf(ra * ra / Raa, rb * rb / Rbb));
+  if (chi2 < cut) chi2 = fmaxf(chi2, fmaxf(ra * ra / Raa, rb * rb / Rbb));
+  return chi2;
+}
+
+// Box test ahead of the chi2: the residuals of hit_chi2 against the
+// half-widths (ha, hb) of the candidate's search window.  Every hit that
+// hit_chi2 accepts passes it: its bound gives r_a^2 < cut R_aa and
+// r_b^2 < cut R_bb, and the window's half-widths bound sqrt(cut R_aa) and
+// sqrt(cut R_bb) from above with a 5% margin.
+__device__ __forceinline__ bool hit_in_box(int kind, float x, float y, float z, const HitRec& h, float ha,
+                                           float hb) {
+  const float along = fmaf(h.c, x, h.s * y);
+  const float ra = fmaf(h.s, x, -h.c * y);
+  const float rb = kind == 0 ? h.w - z : h.w - along;
+  return along > 0.0f && fabsf(ra) < ha && fabsf(rb) < hb;
 }
 
 __device__ __forceinline__ PosState pos_state(const float p[6], const float C[21]) {

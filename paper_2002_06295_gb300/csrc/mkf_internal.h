@@ -98,10 +98,11 @@ struct mkf_ctx {
 
   // binning
   bool binned = false;
+  bool bins_ordered = false;   // each bin sorted by the caller's hit index
   int64_t n_hits = 0;
   int n_events = 0;
   int64_t n_bins_total = 0;
-  mkf::DevBuf rec, perm, bin_off, bin_cnt, keys, ranks, vmax, ev_hit_off, scan_part;
+  mkf::DevBuf rec, rec_orig, perm, bin_off, bin_cnt, keys, ranks, vmax, ev_hit_off, scan_part;
 
   // build / dedup
   mkf::DevBuf seed_ctr, stats, status, dd_head, dd_next, dd_beat, dd_nbeat, dd_state, track_hits;
@@ -133,6 +134,7 @@ struct mkf_ctx {
 
 namespace mkf {
 // launchers (each returns the first CUDA error, or cudaSuccess)
+cudaError_t launch_bin_order(mkf_ctx* ctx, cudaStream_t st);
 cudaError_t launch_bin_hits(mkf_ctx* ctx, const float* xyz, const float* lcov, const int* layer, int64_t n_hits,
                             const int64_t* ev_hit_off, int n_events, cudaStream_t st);
 cudaError_t launch_build(mkf_ctx* ctx, const BuildArgs& a, cudaStream_t st);

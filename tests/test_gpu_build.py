@@ -117,6 +117,30 @@ def test_search_window_is_conservative(cfg):
     ctx.close()
 
 
+def test_results_do_not_depend_on_launch_shape():
+    """The binning granularity, warps per block and lanes per seed change only
+    how the work is spread: the whole C2 event must come out bit-identical
+    (hits, surfaces, parameters, covariances, scores, flags) and the same
+    candidate-hit pairs must reach the chi2."""
+    import paper_2002_06295_gb300 as mkf
+    ev = synth.make_config_event(2)
+    ref = None
+    for nphi, nw, warps, lanes in [(64, 16, 4, 0), (128, 32, 8, 32), (32, 8, 2, 16), (256, 64, 8, 8)]:
+        ctx = make_ctx(ev.geom, nphi, nw)
+        mkf.mkf_set_build_config(ctx, warps, lanes)
+        g = gpu_build(ctx, [ev], max_cands=6)
+        ctx.close()
+        if ref is None:
+            ref = g
+            continue
+        for k in ("hits", "layers", "counts", "flags"):
+            assert np.array_equal(g[k], ref[k]), (k, nphi, nw, warps, lanes)
+        for k in ("par", "cov", "score", "chi2"):
+            assert np.array_equal(g[k], ref[k], equal_nan=True), (k, nphi, nw, warps, lanes)
+        for k in ("cand_steps", "updates", "chi2_full", "nav_tests"):
+            assert g["stats"][k] == ref["stats"][k], (k, nphi, nw, warps, lanes)
+
+
 def test_batched_events_equal_single_events():
     """Uneven events in one launch give bit-identical results to one launch per
     event, and match the oracle per event."""
