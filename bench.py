@@ -400,6 +400,9 @@ def main():
     stream = torch.cuda.current_stream()
     mkf.mkf_set_timing(ctx, True)
 
+    side = torch.cuda.Stream(device=dev)      # the inward fit runs beside the adjoint
+    fwd_done, bwd_done = torch.cuda.Event(), torch.cuda.Event()
+
     def step(inp):
         mkf.mkf_bin_hits(ctx, inp["xyz"], inp["lcov"], inp["layer"], inp["hoff"])
         mkf.mkf_build_tracks(ctx, inp["sp"], inp["sc"], inp["soff"], chi2_cut=spec["chi2_cut"],
@@ -407,13 +410,18 @@ def main():
                              dup_frac=spec["dup_frac"], out=out)
         mkf.mkf_fit_tracks(ctx, inp["xyz"], inp["lcov"], inp["layer"], out["hits"], inp["sp"], inp["sc"],
                            ckpt=ckpt, out=fit_out)
+        fwd_done.record(stream)
+        side.wait_event(fwd_done)
+        mkf.mkf_fit_backward(ctx, inp["xyz"], inp["lcov"], inp["layer"], out["hits"], fit_out["par"], out=bwd_out,
+                             stream=side)
+        bwd_done.record(side)
         if has_adjoint[0]:
             try:
                 mkf.mkf_fit_tracks_adjoint(ctx, inp["xyz"], inp["lcov"], inp["layer"], out["hits"], inp["sp"],
                                            inp["sc"], ckpt, g_chi2=g_chi2, out=adj_out)
             except mkf.MkfError:
                 has_adjoint[0] = False
-        mkf.mkf_fit_backward(ctx, inp["xyz"], inp["lcov"], inp["layer"], out["hits"], fit_out["par"], out=bwd_out)
+        stream.wait_event(bwd_done)
 
     # warm-up
     for _ in range(max(args.warmup, 3) if args.warmup > 0 else 0):

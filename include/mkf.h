@@ -24,6 +24,12 @@
  *    device status word and returned by the next mkf_sync().
  *  - A context is bound to one device and is not thread safe: use one per
  *    host thread.  It owns a workspace that grows on demand (cudaMalloc).
+ *  - Streams: mkf_bin_hits, mkf_build_tracks and mkf_dedup_tracks use the
+ *    context's binning and building workspace, so calls of these on one
+ *    context must be ordered (same stream, or events).  mkf_fit_tracks,
+ *    mkf_fit_backward and mkf_fit_tracks_adjoint touch no workspace: they may
+ *    run concurrently on different streams once their inputs are ready (an
+ *    adjoint next to the inward fit, for instance).
  *  - No C++ exception crosses this interface.
  */
 #ifndef MKF_H

@@ -139,9 +139,16 @@ __device__ __forceinline__ void transport_cov_into(const Jac4<float>& J, const f
   dst[ci(5, 5)] = C[ci(5, 5)] + ms_theta;
 }
 
-__device__ __forceinline__ HitRec load_rec(const float4* __restrict__ rec, int pos) {
-  float4 a = __ldg(&rec[2 * pos]);
-  float4 b = __ldg(&rec[2 * pos + 1]);
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int K> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory");
+}
+
+__device__ __forceinline__ HitRec unpack_rec(const float4 a, const float4 b) {
   HitRec h;
   h.c = a.x;
   h.s = a.y;
@@ -152,6 +159,9 @@ __device__ __forceinline__ HitRec load_rec(const float4* __restrict__ rec, int p
   h.orig = __float_as_int(b.z);
   h.bin = __float_as_int(b.w);
   return h;
+}
+__device__ __forceinline__ HitRec load_rec(const float4* __restrict__ rec, int pos) {
+  return unpack_rec(__ldg(&rec[2 * pos]), __ldg(&rec[2 * pos + 1]));
 }
 
 __device__ __forceinline__ int event_of(const int64_t* off, int n_events, int64_t i) {
@@ -199,7 +209,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
   const unsigned gfull = GS == 32 ? 0xffffffffu : ((1u << GS) - 1u);
   const unsigned gmask = gfull << gbase;
 
-  float* prop = reinterpret_cast<float*>(smem + sizeof(GeomDev));                  // [W][32][kSlotWords]
+  float4* stage = reinterpret_cast<float4*>(smem + sizeof(GeomDev));               // [W][32][2 buffers][2]
+  float* prop = reinterpret_cast<float*>(stage + W * 32 * 4);                       // [W][32][kSlotWords]
   int* win = reinterpret_cast<int*>(prop + W * 32 * kSlotWords);                   // [W][32][kWinWords]
   int* cnt = win + W * 32 * kWinWords;                                              // [W][32]
   int* rowp = cnt + W * 32;                                                         // [W][32]
@@ -209,6 +220,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
   float* bests = reinterpret_cast<float*>(top + W * NG * NMAX);                     // [W][NG][32]
   uint32_t* hist = reinterpret_cast<uint32_t*>(bests + W * NG * 32);                // [W][NG][L][NMAX]
   float* myprop = prop + (warp * 32 + lane) * kSlotWords;
+  float4* mystage = stage + (warp * 32 + lane) * 4;
   float* gprop = prop + (warp * 32 + gbase) * kSlotWords;
   int* mywin = win + (warp * 32 + lane) * kWinWords;
   int* gwin = win + (warp * 32 + gbase) * kWinWords;
@@ -393,8 +405,9 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
     // A window is nb phi rows, each a contiguous range of hits (w bins
     // iw0..iw1).  The rows of all the warp's candidates are dealt to the 32
     // lanes, then the hits of those rows, so every lane's loads are
-    // independent and a seed with a wide window
-    // does not hold up the warp.  Each hit gets the box test, then its chi2 if
+    // independent and a seed with a wide window does not hold up the warp;
+    // each lane's next hit record is copied to shared memory (cp.async) while
+    // it works on the current one.  Each hit gets the box test, then its chi2 if
     // it passes; an accepted child goes straight into its seed's top-N slots.
     if (li < N) gtop[li] = ~0ull;
     __syncwarp();
@@ -434,17 +447,36 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
         rpre[warp * 32 + lane] = hin - len;
         rbc[warp * 32 + lane] = make_int2(beg, cl);
         __syncwarp();
-        for (int h0 = 0; h0 < Hw; h0 += 32) {
-          const int h = h0 + lane;
-          if (h < Hw) {
-            // the row holding flattened hit h: last lane whose hit prefix is <= h
-            int j = 0;
+        // the row holding flattened hit h: last lane whose hit prefix is <= h
+        auto locate = [&](int h, int& cc, int& pos) {
+          int j = 0;
 #pragma unroll
-            for (int st = 16; st > 0; st >>= 1)
-              if (wpre[j + st] <= h) j += st;
-            const int2 bc = wbc[j];
-            const int cc = bc.y;
-            const HitRec hr = load_rec(a.rec, bc.x + (h - wpre[j]));
+          for (int st = 16; st > 0; st >>= 1)
+            if (wpre[j + st] <= h) j += st;
+          const int2 bc = wbc[j];
+          cc = bc.y;
+          pos = bc.x + (h - wpre[j]);
+        };
+        // a lane's next record is copied to shared memory while it works on the current one
+        int cc_n = -1, pos_n = 0;
+        if (lane < Hw) {
+          locate(lane, cc_n, pos_n);
+          cp_async16(mystage, a.rec + 2 * pos_n);
+          cp_async16(mystage + 1, a.rec + 2 * pos_n + 1);
+        }
+        cp_async_commit();
+        for (int h0 = 0, buf = 0; h0 < Hw; h0 += 32, buf ^= 2) {
+          const int cc = cc_n;
+          cc_n = -1;
+          if (h0 + 32 + lane < Hw) {
+            locate(h0 + 32 + lane, cc_n, pos_n);
+            cp_async16(mystage + (buf ^ 2), a.rec + 2 * pos_n);
+            cp_async16(mystage + (buf ^ 2) + 1, a.rec + 2 * pos_n + 1);
+          }
+          cp_async_commit();
+          cp_async_wait<1>();
+          if (cc >= 0) {
+            const HitRec hr = unpack_rec(mystage[buf], mystage[buf + 1]);
             const int* wd = wwin + cc * kWinWords;
             const float* ps = wprop + cc * kSlotWords;
             const int kind = wd[0];
@@ -463,6 +495,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
             }
           }
         }
+        cp_async_wait<0>();
         __syncwarp();
       }
     }
@@ -621,7 +654,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
 template <int NMAX>
 size_t build_smem(int L, int W, int GS) {
   const int NG = 32 / GS;
-  return sizeof(GeomDev) + (size_t)W * 32 * (kSlotWords + kWinWords + 1 + 4) * 4 + (size_t)W * NG * NMAX * 8 +
+  return sizeof(GeomDev) + (size_t)W * 32 * 64 + (size_t)W * 32 * (kSlotWords + kWinWords + 1 + 4) * 4 +
+         (size_t)W * NG * NMAX * 8 +
          (size_t)W * NG * 32 * 4 +
          (size_t)W * NG * L * NMAX * 4;
 }

@@ -4,8 +4,9 @@
 //
 // The outward fit runs in FP32.  The inward fit starts from a prior 100 times
 // wider than the seed's, so its first updates shrink variances by factors up
-// to 1e5; FP32 cannot carry those cancellations to 1e-4, so it runs in FP64
-// (the inward fit is a few percent of the path's work).
+// to 1e5; FP32 cannot carry those cancellations to 1e-4, so the first
+// kInwardFp64Updates updates run in FP64.  By then the state is constrained
+// and the rest of the inward fit runs in FP32 like the outward fit.
 #include "mkf_device.cuh"
 #include "mkf_fit_common.cuh"
 #include "mkf_internal.h"
@@ -15,7 +16,7 @@ namespace mkf {
 namespace {
 
 template <class T>
-__global__ void k_fit(const GeomDev* __restrict__ g, int dir, const float* __restrict__ xyz,
+__global__ void k_fit(const GeomDev* __restrict__ g, const float* __restrict__ xyz,
                       const float* __restrict__ lcov, const int* __restrict__ layer, int64_t H,
                       const int* __restrict__ hits, int K, const float* __restrict__ init_par,
                       const float* __restrict__ init_cov, int64_t NT, const float* __restrict__ align,
@@ -30,60 +31,100 @@ __global__ void k_fit(const GeomDev* __restrict__ g, int dir, const float* __res
   T chi2(0.0);
   int ok = 1;
   const int* row = hits + t * K;
-  if (dir > 0) {
 #pragma unroll
-    for (int k = 0; k < 21; ++k) C[k] = T(init_cov[k * NT + t]);
-    for (int k = 0; k < K; ++k) {
-      if (ckpt) {
-        float* c = ckpt + (size_t)k * 27 * NT + t;
+  for (int k = 0; k < 21; ++k) C[k] = T(init_cov[k * NT + t]);
+  for (int k = 0; k < K; ++k) {
+    if (ckpt) {
+      float* c = ckpt + (size_t)k * 27 * NT + t;
 #pragma unroll
-        for (int i = 0; i < 6; ++i) c[i * NT] = float(p[i]);
+      for (int i = 0; i < 6; ++i) c[i * NT] = float(p[i]);
 #pragma unroll
-        for (int i = 0; i < 21; ++i) c[(6 + i) * NT] = float(C[i]);
-      }
-      FitHit<T> f;
-      if (!load_fit_hit(g, xyz, lcov, layer, H, row[k], align, x0, f)) continue;
-      if (!step_to(f, p, C, ck, +1)) {
-        ok = 0;
-        // mark the steps that did not happen (x = NaN) for the adjoint
-        if (ckpt)
-          for (int k2 = k; k2 < K; ++k2) ckpt[(size_t)k2 * 27 * NT + t] = __int_as_float(0x7fc00000);
-        break;
-      }
-      chi2 += kf_update(f.kind, p, C, f.m);
+      for (int i = 0; i < 21; ++i) c[(6 + i) * NT] = float(C[i]);
     }
-  } else {
-    // inward: covariance reset to 100 x the seed-style diagonal, update with
-    // the outermost hit in place, then propagate inward hit by hit
-#pragma unroll
-    for (int k = 0; k < 21; ++k) C[k] = T(0.0);
-    C[ci(0, 0)] = C[ci(1, 1)] = C[ci(2, 2)] = T(1.0);
-    C[ci(3, 3)] = T(100.0) * (T(0.05) * p[3]) * (T(0.05) * p[3]);
-    C[ci(4, 4)] = C[ci(5, 5)] = T(0.25);
-    int last = -1;
-    for (int k = K - 1; k >= 0; --k)
-      if (row[k] >= 0) {
-        last = k;
-        break;
-      }
-    if (last >= 0) {
-      FitHit<T> f;
-      if (load_fit_hit(g, xyz, lcov, layer, H, row[last], align, x0, f)) chi2 += kf_update(f.kind, p, C, f.m);
-      for (int k = last - 1; k >= 0; --k) {
-        if (!load_fit_hit(g, xyz, lcov, layer, H, row[k], align, x0, f)) continue;
-        if (!step_to(f, p, C, ck, -1)) {
-          ok = 0;
-          break;
-        }
-        chi2 += kf_update(f.kind, p, C, f.m);
-      }
+    FitHit<T> f;
+    if (!load_fit_hit(g, xyz, lcov, layer, H, row[k], align, x0, f)) continue;
+    if (!step_to(f, p, C, ck, +1)) {
+      ok = 0;
+      // mark the steps that did not happen (x = NaN) for the adjoint
+      if (ckpt)
+        for (int k2 = k; k2 < K; ++k2) ckpt[(size_t)k2 * 27 * NT + t] = __int_as_float(0x7fc00000);
+      break;
     }
+    chi2 += kf_update(f.kind, p, C, f.m);
   }
 #pragma unroll
   for (int k = 0; k < 6; ++k) out_par[k * NT + t] = float(p[k]);
 #pragma unroll
   for (int k = 0; k < 21; ++k) out_cov[k * NT + t] = float(C[k]);
   out_chi2[t] = float(chi2);
+  if (out_ok) out_ok[t] = ok;
+}
+
+constexpr int kInwardFp64Updates = 4;
+
+// Inward fit: covariance reset to 100 x the seed-style diagonal, update with
+// the outermost hit in place, then propagate inward hit by hit.
+__global__ void k_fit_inward(const GeomDev* __restrict__ g, const float* __restrict__ xyz,
+                             const float* __restrict__ lcov, const int* __restrict__ layer, int64_t H,
+                             const int* __restrict__ hits, int K, const float* __restrict__ init_par, int64_t NT,
+                             const float* __restrict__ align, const float* __restrict__ x0,
+                             float* __restrict__ out_par, float* __restrict__ out_cov, float* __restrict__ out_chi2,
+                             int* __restrict__ out_ok) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= NT) return;
+  const int* row = hits + t * K;
+  double pd[6], Cd[21];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) pd[k] = double(init_par[k * NT + t]);
+#pragma unroll
+  for (int k = 0; k < 21; ++k) Cd[k] = 0.0;
+  Cd[ci(0, 0)] = Cd[ci(1, 1)] = Cd[ci(2, 2)] = 1.0;
+  Cd[ci(3, 3)] = 100.0 * (0.05 * pd[3]) * (0.05 * pd[3]);
+  Cd[ci(4, 4)] = Cd[ci(5, 5)] = 0.25;
+  int last = -1;
+  for (int k = K - 1; k >= 0; --k)
+    if (row[k] >= 0) {
+      last = k;
+      break;
+    }
+  double chi2d = 0.0;
+  int ok = 1, k = last, done = 0;
+  {
+    const double ck = double(g->c_kappa);
+    FitHit<double> f;
+    for (; k >= 0 && done < kInwardFp64Updates; --k) {
+      if (!load_fit_hit(g, xyz, lcov, layer, H, row[k], align, x0, f)) continue;
+      if (k != last && !step_to(f, pd, Cd, ck, -1)) {
+        ok = 0;
+        break;
+      }
+      chi2d += kf_update(f.kind, pd, Cd, f.m);
+      ++done;
+    }
+  }
+  float p[6], C[21];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) p[i] = float(pd[i]);
+#pragma unroll
+  for (int i = 0; i < 21; ++i) C[i] = float(Cd[i]);
+  float chi2 = 0.0f;
+  if (ok) {
+    const float ck = g->c_kappa;
+    FitHit<float> f;
+    for (; k >= 0; --k) {
+      if (!load_fit_hit(g, xyz, lcov, layer, H, row[k], align, x0, f)) continue;
+      if (k != last && !step_to(f, p, C, ck, -1)) {
+        ok = 0;
+        break;
+      }
+      chi2 += kf_update(f.kind, p, C, f.m);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 6; ++i) out_par[i * NT + t] = p[i];
+#pragma unroll
+  for (int i = 0; i < 21; ++i) out_cov[i * NT + t] = C[i];
+  out_chi2[t] = float(chi2d + double(chi2));
   if (out_ok) out_ok[t] = ok;
 }
 
@@ -101,13 +142,11 @@ cudaError_t launch_fit(mkf_ctx* ctx, int direction, const float* xyz, const floa
   const unsigned grid = (unsigned)((n_tracks + T - 1) / T);
   ctx->tick(tid, st);
   if (direction > 0)
-    k_fit<float><<<grid, T, 0, st>>>(ctx->geom_dev.as<GeomDev>(), direction, xyz, lcov, layer, n_hits, hits, K,
-                                     init_par, init_cov, n_tracks, align, x0, out_par, out_cov, out_chi2, out_ok,
-                                     ckpt);
+    k_fit<float><<<grid, T, 0, st>>>(ctx->geom_dev.as<GeomDev>(), xyz, lcov, layer, n_hits, hits, K, init_par,
+                                     init_cov, n_tracks, align, x0, out_par, out_cov, out_chi2, out_ok, ckpt);
   else
-    k_fit<double><<<grid, T, 0, st>>>(ctx->geom_dev.as<GeomDev>(), direction, xyz, lcov, layer, n_hits, hits, K,
-                                      init_par, init_cov, n_tracks, align, x0, out_par, out_cov, out_chi2, out_ok,
-                                      nullptr);
+    k_fit_inward<<<grid, T, 0, st>>>(ctx->geom_dev.as<GeomDev>(), xyz, lcov, layer, n_hits, hits, K, init_par,
+                                     n_tracks, align, x0, out_par, out_cov, out_chi2, out_ok);
   ctx->tock(tid, st);
   return cudaGetLastError();
 }
