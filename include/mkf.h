@@ -147,6 +147,15 @@ mkf_status mkf_build_tracks(mkf_ctx* ctx, const float* seed_par, const float* se
  * (paper_2002_06295_gb300/tune.py); it changes speed only, never results. */
 mkf_status mkf_set_build_config(mkf_ctx* ctx, int warps_per_block, int lanes_per_seed);
 
+/* Launch shape of mkf_fit_tracks_adjoint: lanes_per_track 1 (one thread per
+ * track), 8 (eight lanes per track share the dual-number passes), or 0 =
+ * choose by the number of tracks (8 below 128 tracks per SM).  The paper has
+ * no counterpart (the adjoint is not in the paper).  Speed only: both shapes
+ * compute the same contribution of every track bit for bit (sums over tracks
+ * are accumulated by atomics, so they agree to rounding).  MKF_ERR_ARG for any
+ * other value. */
+mkf_status mkf_set_adjoint_config(mkf_ctx* ctx, int lanes_per_track);
+
 /* Debug switch for mkf_build_tracks: when on, every candidate step also
  * evaluates chi2 against every hit of the layer and counts accepted hits that
  * lay outside its search window (statistic 4 of mkf_get_stats; it must be 0). */

@@ -25,6 +25,7 @@ SIGNATURES = {
     "mkf_build_tracks": (i32, [P, P, P, P, i64, f32, i32, i32, i32, f32, P, P, P, P, P, P, P, P, P]),
     "mkf_set_debug": (i32, [P, i32]),
     "mkf_set_build_config": (i32, [P, i32, i32]),
+    "mkf_set_adjoint_config": (i32, [P, i32]),
     "mkf_get_stats": (i32, [P, P, i32, P]),
     "mkf_set_timing": (i32, [P, i32]),
     "mkf_get_timings": (i32, [P, P, i32, P]),

@@ -197,6 +197,14 @@ mkf_status mkf_set_build_config(mkf_ctx* ctx, int warps_per_block, int lanes_per
   return MKF_OK;
 }
 
+mkf_status mkf_set_adjoint_config(mkf_ctx* ctx, int lanes_per_track) {
+  if (check_ctx(ctx)) return MKF_ERR_ARG;
+  if (lanes_per_track != 0 && lanes_per_track != 1 && lanes_per_track != 8)
+    return ctx->fail(MKF_ERR_ARG, "lanes_per_track must be 0, 1 or 8");
+  ctx->adjoint_lanes = lanes_per_track;
+  return MKF_OK;
+}
+
 mkf_status mkf_set_debug(mkf_ctx* ctx, int brute_force_window_check) {
   if (check_ctx(ctx)) return MKF_ERR_ARG;
   ctx->debug_window = brute_force_window_check ? 1 : 0;

@@ -4,7 +4,11 @@
 // with respect to hit positions, per-layer alignment (dr, dphi, dz) and
 // per-layer thickness.
 //
-// One thread per track sweeps its steps backwards.  Each step is recomputed
+// One thread per track, or a group of 8 lanes per track when there are few
+// tracks (lane e then runs dual pass e of steps (2) and (4) below and the
+// lanes exchange the results by shuffles; everything else is computed by every
+// lane of the group, so each track's contribution is the same bit for bit),
+// sweeps the track's steps backwards.  Each step is recomputed
 // from the checkpoint written by the forward fit (state before the step),
 // then the adjoint is pushed back through
 //   (1) the Kalman update  p_k = p + K r, C_k = C - B W B^T, chi2 = r^T W r
@@ -33,6 +37,53 @@ constexpr int kAdjThreads = 128;
 
 __device__ __forceinline__ float Gf(const float G[21], int i, int j) { return G[ci(i, j)]; }
 
+// derivative of g44 C_phiphi + g55 C_thetatheta (material term) along input w_
+// of theta0^2: pp x (0), y (1), kappa (3), phi (4), theta (5), thickness (6)
+__device__ __forceinline__ float material_pass(int w_, const float pp[6], const FitHit<float>& f, float g44,
+                                               float g55) {
+  DF X(pp[0], w_ == 0 ? 1.f : 0.f), Y(pp[1], w_ == 1 ? 1.f : 0.f), KA(pp[3], w_ == 3 ? 1.f : 0.f);
+  DF PH(pp[4], w_ == 4 ? 1.f : 0.f), TH(pp[5], w_ == 5 ? 1.f : 0.f), X0(f.x0, w_ == 6 ? 1.f : 0.f);
+  DF sp, cph, st, ct;
+  msincos(PH, &sp, &cph);
+  msincos(TH, &st, &ct);
+  const DF th2 = highland_theta0_sq(f.kind, X0, X, Y, cph, sp, KA, st, ct);
+  const DF q44 = th2 / (st * st);
+  return fmaf(g44, q44.d, g55 * th2.d);
+}
+
+// p0bar_e = sum_i ppbar_i dpp_i/de + sum Jbar . dJ/de along input e of the
+// propagation: p0[0..5] (e < 6) or the surface position (e = 6)
+__device__ __forceinline__ float prop_pass(int e, const float p0[6], const FitHit<float>& f, float ck,
+                                           const float ppb[6], const float Jb[4][6]) {
+  DF q[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) q[i] = DF(p0[i], e == i ? 1.f : 0.f);
+  const DF posd(f.pos, e == 6 ? 1.f : 0.f);
+  DF st, ct;
+  msincos(q[5], &st, &ct);
+  const DF cot = ct / st;
+  const DF om = DF(ck) * q[3];
+  DF sd;
+  if (f.kind == 0) {
+    DF sph, cph;
+    msincos(q[4], &sph, &cph);
+    sd = cylinder_path(q[0], q[1], cph, sph, om, posd, +1);
+  } else {
+    sd = plane_path(q[2], cot, posd, +1);
+  }
+  const auto hd = helix_at(q[0], q[1], q[2], q[4], cot, om, sd);
+  const auto Jd = transport_jacobian(f.kind, q, hd, sd, om, DF(ck), cot, st);
+  float acc_e = fmaf(ppb[0], hd.x.d, fmaf(ppb[1], hd.y.d, fmaf(ppb[2], hd.z.d, ppb[4] * hd.phi.d)));
+  if (e == 3) acc_e += ppb[3];
+  if (e == 5) acc_e += ppb[5];
+#pragma unroll
+  for (int qq = 0; qq < 4; ++qq)
+#pragma unroll
+    for (int j = 0; j < 6; ++j) acc_e = fmaf(Jb[qq][j], Jd.r[qq][j].d, acc_e);
+  return acc_e;
+}
+
+template <int LPT>
 __global__ void __launch_bounds__(kAdjThreads)
     k_fit_adjoint(const GeomDev* __restrict__ g, const float* __restrict__ xyz, const float* __restrict__ lcov,
                   const int* __restrict__ layer, int64_t H, const int* __restrict__ hits, int K, int64_t NT,
@@ -43,7 +94,10 @@ __global__ void __launch_bounds__(kAdjThreads)
   const int L = g->n_layers;
   for (int i = threadIdx.x; i < L * 4; i += blockDim.x) acc[i] = 0.0f;
   __syncthreads();
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / LPT;
+  const int sub = threadIdx.x % LPT;                         // lane in the track's group
+  const int gbase = (threadIdx.x & 31) - sub;
+  const unsigned gm = LPT == 32 ? 0xffffffffu : ((1u << LPT) - 1u) << gbase;
   if (t < NT) {
     const float ck = g->c_kappa;
     float pb[6], G[21];
@@ -223,23 +277,26 @@ __global__ void __launch_bounds__(kAdjThreads)
       float x0b = 0.f;
       if (mat) {
         const float g44 = G2[ci(4, 4)], g55 = G2[ci(5, 5)];
-        // inputs of theta0^2: pp x (0), y (1), kappa (3), phi (4), theta (5), thickness (6)
         constexpr int kIn[6] = {0, 1, 3, 4, 5, 6};
+        if (LPT == 1) {
 #pragma unroll
-        for (int e = 0; e < 6; ++e) {
-          const int w_ = kIn[e];
-          DF X(pp[0], w_ == 0 ? 1.f : 0.f), Y(pp[1], w_ == 1 ? 1.f : 0.f), KA(pp[3], w_ == 3 ? 1.f : 0.f);
-          DF PH(pp[4], w_ == 4 ? 1.f : 0.f), TH(pp[5], w_ == 5 ? 1.f : 0.f), X0(f.x0, w_ == 6 ? 1.f : 0.f);
-          DF sp, cph, st, ct;
-          msincos(PH, &sp, &cph);
-          msincos(TH, &st, &ct);
-          const DF th2 = highland_theta0_sq(f.kind, X0, X, Y, cph, sp, KA, st, ct);
-          const DF q44 = th2 / (st * st);
-          const float dF = fmaf(g44, q44.d, g55 * th2.d);
-          if (w_ == 6)
-            x0b = dF;
-          else
-            ppb[w_] += dF;
+          for (int e = 0; e < 6; ++e) {
+            const float dF = material_pass(kIn[e], pp, f, g44, g55);
+            if (kIn[e] == 6)
+              x0b = dF;
+            else
+              ppb[kIn[e]] += dF;
+          }
+        } else {
+          const float dF = material_pass(kIn[sub < 6 ? sub : 0], pp, f, g44, g55);
+#pragma unroll
+          for (int e = 0; e < 6; ++e) {
+            const float v = __shfl_sync(gm, dF, gbase + e);
+            if (kIn[e] == 6)
+              x0b = v;
+            else
+              ppb[kIn[e]] += v;
+          }
         }
       }
 
@@ -289,40 +346,22 @@ __global__ void __launch_bounds__(kAdjThreads)
         }
 
       // ---------------- (4) reverse of the propagation (dual passes)
-      // p0bar_e = sum_i ppbar_i dpp_i/de + sum Jbar . dJ/de,  e = p0[0..5], surface
       float p0b[6];
       float posb = 0.f;
+      if (LPT == 1) {
 #pragma unroll 1
-      for (int e = 0; e < 7; ++e) {
-        DF q[6];
-#pragma unroll
-        for (int i = 0; i < 6; ++i) q[i] = DF(p0[i], e == i ? 1.f : 0.f);
-        const DF posd(f.pos, e == 6 ? 1.f : 0.f);
-        DF st, ct;
-        msincos(q[5], &st, &ct);
-        const DF cot = ct / st;
-        const DF om = DF(ck) * q[3];
-        DF sd;
-        if (f.kind == 0) {
-          DF sph, cph;
-          msincos(q[4], &sph, &cph);
-          sd = cylinder_path(q[0], q[1], cph, sph, om, posd, +1);
-        } else {
-          sd = plane_path(q[2], cot, posd, +1);
+        for (int e = 0; e < 7; ++e) {
+          const float acc_e = prop_pass(e, p0, f, ck, ppb, Jb);
+          if (e < 6)
+            p0b[e] = acc_e;
+          else
+            posb = acc_e;
         }
-        const auto hd = helix_at(q[0], q[1], q[2], q[4], cot, om, sd);
-        const auto Jd = transport_jacobian(f.kind, q, hd, sd, om, DF(ck), cot, st);
-        float acc_e = fmaf(ppb[0], hd.x.d, fmaf(ppb[1], hd.y.d, fmaf(ppb[2], hd.z.d, ppb[4] * hd.phi.d)));
-        if (e == 3) acc_e += ppb[3];
-        if (e == 5) acc_e += ppb[5];
+      } else {
+        const float acc_e = prop_pass(sub < 7 ? sub : 0, p0, f, ck, ppb, Jb);
 #pragma unroll
-        for (int qq = 0; qq < 4; ++qq)
-#pragma unroll
-          for (int j = 0; j < 6; ++j) acc_e = fmaf(Jb[qq][j], Jd.r[qq][j].d, acc_e);
-        if (e < 6)
-          p0b[e] = acc_e;
-        else
-          posb = acc_e;
+        for (int e = 0; e < 6; ++e) p0b[e] = __shfl_sync(gm, acc_e, gbase + e);
+        posb = __shfl_sync(gm, acc_e, gbase + 6);
       }
 
       // ---------------- (5) hit frame and surface back to hit xyz and alignment
@@ -342,14 +381,16 @@ __global__ void __launch_bounds__(kAdjThreads)
         gdr += wb;
         gdz += posb;
       }
-      atomicAdd(&g_hit[h], gx);
-      atomicAdd(&g_hit[H + h], gy);
-      atomicAdd(&g_hit[2 * H + h], gz);
-      const int l = f.layer;
-      atomicAdd(&acc[4 * l + 0], gdr);
-      atomicAdd(&acc[4 * l + 1], phib);
-      atomicAdd(&acc[4 * l + 2], gdz);
-      atomicAdd(&acc[4 * l + 3], x0b);
+      if (sub == 0) {
+        atomicAdd(&g_hit[h], gx);
+        atomicAdd(&g_hit[H + h], gy);
+        atomicAdd(&g_hit[2 * H + h], gz);
+        const int l = f.layer;
+        atomicAdd(&acc[4 * l + 0], gdr);
+        atomicAdd(&acc[4 * l + 1], phib);
+        atomicAdd(&acc[4 * l + 2], gdz);
+        atomicAdd(&acc[4 * l + 3], x0b);
+      }
 
       // adjoints of the state before this step
 #pragma unroll
@@ -386,11 +427,22 @@ cudaError_t launch_fit_adjoint(mkf_ctx* ctx, const float* xyz, const float* lcov
   if ((e = cudaMemsetAsync(g_x0, 0, (size_t)L * sizeof(float), st))) return e;
   if (n_tracks == 0) return cudaSuccess;
   ctx->tick(kTAdjoint, st);
-  const int T = n_tracks >= (int64_t)ctx->n_sm * kAdjThreads ? kAdjThreads
-              : (n_tracks >= (int64_t)ctx->n_sm * 64 ? 64 : 32);
-  k_fit_adjoint<<<(unsigned)((n_tracks + T - 1) / T), T, 0, st>>>(
-      ctx->geom_dev.as<GeomDev>(), xyz, lcov, layer, n_hits, hits, K, n_tracks, align, x0, ckpt, g_chi2, g_par, g_cov,
-      g_hit, g_align, g_x0);
+  // few tracks: 8 lanes per track spread the dual passes and give the SMs
+  // enough warps; many tracks: one thread per track does the least work
+  int lpt = ctx->adjoint_lanes;
+  if (lpt != 1 && lpt != 8) lpt = n_tracks < (int64_t)ctx->n_sm * kAdjThreads ? 8 : 1;
+  if (lpt == 8) {
+    const int64_t threads = n_tracks * 8;
+    k_fit_adjoint<8><<<(unsigned)((threads + kAdjThreads - 1) / kAdjThreads), kAdjThreads, 0, st>>>(
+        ctx->geom_dev.as<GeomDev>(), xyz, lcov, layer, n_hits, hits, K, n_tracks, align, x0, ckpt, g_chi2, g_par,
+        g_cov, g_hit, g_align, g_x0);
+  } else {
+    const int T = n_tracks >= (int64_t)ctx->n_sm * kAdjThreads ? kAdjThreads
+                : (n_tracks >= (int64_t)ctx->n_sm * 64 ? 64 : 32);
+    k_fit_adjoint<1><<<(unsigned)((n_tracks + T - 1) / T), T, 0, st>>>(
+        ctx->geom_dev.as<GeomDev>(), xyz, lcov, layer, n_hits, hits, K, n_tracks, align, x0, ckpt, g_chi2, g_par,
+        g_cov, g_hit, g_align, g_x0);
+  }
   ctx->tock(kTAdjoint, st);
   return cudaGetLastError();
 }

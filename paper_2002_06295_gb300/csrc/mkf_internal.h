@@ -95,6 +95,7 @@ struct mkf_ctx {
   int debug_window = 0;
   int build_warps = 4;   // warps per block of the building kernel
   int build_group = 0;   // lanes per seed (0: max_cands rounded up to a power of two)
+  int adjoint_lanes = 0; // lanes per track of the fit adjoint (0: by track count)
 
   // binning
   bool binned = false;

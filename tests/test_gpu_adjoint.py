@@ -82,6 +82,37 @@ def test_adjoint_matches_oracle_gradient(upstream):
     ctx.close()
 
 
+def test_adjoint_launch_shapes_agree():
+    """One thread per track and eight lanes per track compute the same
+    per-track adjoint: hit gradients (each hit here belongs to one track) are
+    equal bit for bit; layer sums, accumulated by atomics in launch order,
+    agree to rounding."""
+    import paper_2002_06295_gb300 as mkf
+    g, ev, hits, sp, sc, align, x0, up = _inputs(n=500, seed=24)
+    dev = torch.device("cuda", 0)
+    ctx = make_ctx(g)
+    T, K = hits.shape
+    xyz_d, lcov_d, lay_d, hits_d = f32(ev.hit_xyz.T, dev), f32(ev.hit_lcov.T, dev), i32(ev.hit_layer, dev), i32(hits, dev)
+    sp_d, sc_d, al_d, x0_d = f32(sp.T, dev), f32(sc.T, dev), f32(align, dev), f32(x0, dev)
+    ckpt = torch.empty((K, 27, T), dtype=torch.float32, device=dev)
+    mkf.mkf_fit_tracks(ctx, xyz_d, lcov_d, lay_d, hits_d, sp_d, sc_d, align=al_d, x0=x0_d, ckpt=ckpt)
+    gd = {k: f32(v.T if v.ndim == 2 else v, dev) for k, v in up.items()}
+    res = {}
+    for lanes in (1, 8):
+        mkf.mkf_set_adjoint_config(ctx, lanes)
+        out = mkf.mkf_fit_tracks_adjoint(ctx, xyz_d, lcov_d, lay_d, hits_d, sp_d, sc_d, ckpt, align=al_d, x0=x0_d,
+                                         **gd)
+        mkf.mkf_sync(ctx)
+        res[lanes] = {k: v.cpu().numpy().astype(np.float64) for k, v in out.items()}
+    assert np.array_equal(res[1]["g_hit"], res[8]["g_hit"])
+    for k in ("g_align", "g_x0"):
+        a, b = res[1][k], res[8][k]
+        assert np.abs(a - b).max() <= 1e-5 * np.abs(a).max(), k
+    with pytest.raises(mkf.MkfError):
+        mkf.mkf_set_adjoint_config(ctx, 4)
+    ctx.close()
+
+
 def test_adjoint_matches_central_differences():
     """FP64 central differences of the oracle's fit, h = 1e-6, on a few inputs."""
     import oracle
