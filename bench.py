@@ -316,6 +316,41 @@ def measure_fit_gradient(mkf, dev, reps=3):
             "ms": ms, "fit_gradient_tracks_per_s": T / (ms * 1e-3)}
 
 
+KERNEL_SOURCES = ("paper_2002_06295_gb300/csrc/build.cu", "paper_2002_06295_gb300/csrc/mkf_device.cuh",
+                  "paper_2002_06295_gb300/csrc/mkf_internal.h")
+
+
+def kernel_digest():
+    """sha1 over the building kernel's sources: a profile's counters apply only
+    to the kernel they were taken on."""
+    import hashlib
+    h = hashlib.sha1()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def profiled_traffic(workload):
+    """DRAM bytes (read + write) per launch of the building kernel from the ncu
+    summary committed under profiles/, or None when the summary is missing or
+    was taken on other kernel sources."""
+    path = os.path.join(ROOT, "profiles", "k_build_%s_ncu.md" % workload)
+    try:
+        with open(path) as f:
+            lines = f.read().splitlines()
+    except OSError:
+        return None
+    kv = {}
+    for ln in lines:
+        if ln.startswith("kernel-source-sha1:") or ln.startswith("dram-bytes-per-launch:"):
+            k, v = ln.split(":", 1)
+            kv[k] = v.strip()
+    if kv.get("kernel-source-sha1") != kernel_digest() or "dram-bytes-per-launch" not in kv:
+        return None
+    return int(kv["dram-bytes-per-launch"])
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -519,7 +554,8 @@ def main():
                      "backward": statistics.mean(bwd_ms)},
         "work": stats,
         "roofline": {"kernel": "k_build (combinatorial building)", "bound": "alu", "achieved": achieved,
-                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": profiled_traffic(args.workload),
                      "peak_basis": "FP32: %d SMs x %d lanes x 2 x %.0f MHz" % (props.multi_processor_count,
                                                                                FP32_LANES, max_mhz),
                      "algorithmic_flops_per_launch": alg_flops},
