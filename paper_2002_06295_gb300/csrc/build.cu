@@ -40,6 +40,13 @@ constexpr int kSlotWords = 33;
 // per-lane window: kind, base bin, nphi, nw, b0, nb, iw0, iw1, ha, hb, hit base (+2 pad, odd stride)
 constexpr int kWinWords = 13;
 constexpr uint32_t kHoleKey = 0x0FFFFFFFu;
+// block-level sharing of wide scans (see the kernel): a job has fewer than 2^16
+// hit rounds (the round count shares a word with the job's epoch); every wait
+// is bounded
+constexpr int kJobMaxRounds = 1 << 16;
+constexpr int kJobClaimTries = 256;
+constexpr int kOwnerWaitLimit = 1 << 22;
+constexpr int kHelperPollLimit = 1 << 24;
 constexpr uint32_t kHistHole = 0x3FFFFFu;  // 22-bit local hit index field
 
 struct BuildDev {
@@ -190,6 +197,19 @@ template <int NMAX, bool DEBUG>
 __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
   extern __shared__ __align__(16) unsigned char smem[];
   GeomDev& G = *reinterpret_cast<GeomDev*>(smem);
+  // shared scan jobs, one per warp: next = epoch << 16 | rounds claimed
+  __shared__ int job_next[kMaxWarps], job_total[kMaxWarps], job_hw[kMaxWarps], job_done[kMaxWarps];
+  __shared__ int n_idle, n_alive;
+  if (threadIdx.x < kMaxWarps) {
+    job_next[threadIdx.x] = 0;
+    job_total[threadIdx.x] = 0;
+    job_hw[threadIdx.x] = 0;
+    job_done[threadIdx.x] = 0;
+  }
+  if (threadIdx.x == 0) {
+    n_idle = 0;
+    n_alive = blockDim.x >> 5;
+  }
   {
     const int4* src = reinterpret_cast<const int4*>(a.geom);
     int4* dst = reinterpret_cast<int4*>(smem);
@@ -228,7 +248,6 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
   const int* wpre = rpre + warp * 32;
   const int2* wbc = rbc + warp * 32;
   const int* wwin = win + warp * 32 * kWinWords;
-  const float* wprop = prop + warp * 32 * kSlotWords;
   float* best = bests + (warp * NG + gi) * 32;
   unsigned long long* wtop = top + warp * NG * NMAX;
   unsigned long long* gtop = wtop + gi * NMAX;
@@ -279,6 +298,68 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
     }
   };
   fetch(true);
+
+  // One candidate-hit pair of warp ow's scan: box test, chi2, and an accepted
+  // child into the seed's top-N slots (any warp of the block may run it).
+  auto scan_pair = [&](int ow, int cc, const HitRec& hr) {
+    const int* wd = win + (ow * 32 + cc) * kWinWords;
+    const float* ps = prop + (ow * 32 + cc) * kSlotWords;
+    const int kind = wd[0];
+    ++n_chi2;
+    if (hit_in_box(kind, ps[0], ps[1], ps[2], hr, __int_as_float(wd[8]), __int_as_float(wd[9]))) {
+      ++n_full;
+      const PosState q{ps[0], ps[1], ps[2], ps[6 + ci(0, 0)], ps[6 + ci(1, 0)], ps[6 + ci(1, 1)],
+                       ps[6 + ci(2, 0)], ps[6 + ci(2, 1)], ps[6 + ci(2, 2)]};
+      const float chi2 = hit_chi2(kind, q, hr, cut);
+      if (chi2 < cut) {
+        atomicAdd(&cnt[ow * 32 + cc], 1);
+        const uint32_t hloc = (uint32_t)(hr.orig - wd[10]);
+        top_insert(top + (ow * NG + cc / GS) * NMAX, N,
+                   child_key(ps[27] + 10.0f - chi2, cc & (GS - 1), hloc < kHoleKey ? hloc : kHoleKey - 1));
+      }
+    }
+  };
+  // Claim hit rounds of warp ow's published job and scan them until none is
+  // left; the rounds done are then added to the job's count.  A claim is a CAS
+  // on (epoch, rounds claimed): a stale read of a finished job fails the CAS.
+  auto work_job = [&](int ow) {
+    int processed = 0;
+    for (int it = 0; it < kJobMaxRounds; ++it) {
+      int r = -1, hw = 0;
+      if (lane == 0) {
+        for (int tries = 0; tries < kJobClaimTries; ++tries) {
+          const int v = *reinterpret_cast<volatile int*>(&job_next[ow]);
+          __threadfence_block();
+          const int tot = *reinterpret_cast<volatile int*>(&job_total[ow]);
+          if ((v & 0xFFFF) >= tot) break;
+          hw = *reinterpret_cast<volatile int*>(&job_hw[ow]);
+          if (atomicCAS(&job_next[ow], v, v + 1) == v) {
+            r = v & 0xFFFF;
+            break;
+          }
+        }
+      }
+      r = __shfl_sync(0xffffffffu, r, 0);
+      hw = __shfl_sync(0xffffffffu, hw, 0);
+      if (r < 0) break;
+      const int h = r * 32 + lane;
+      if (h < hw) {
+        const int* opre = rpre + ow * 32;
+        int j = 0;
+#pragma unroll
+        for (int st = 16; st > 0; st >>= 1)
+          if (opre[j + st] <= h) j += st;
+        const int2 bc = rbc[ow * 32 + j];
+        scan_pair(ow, bc.y, load_rec(a.rec, bc.x + (h - opre[j])));
+      }
+      ++processed;
+    }
+    __syncwarp();
+    if (lane == 0 && processed > 0) {
+      __threadfence_block();
+      atomicAdd(&job_done[ow], processed);
+    }
+  };
 
   for (;;) {
     if (__all_sync(0xffffffffu, seed < 0)) break;
@@ -447,6 +528,38 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
         rpre[warp * 32 + lane] = hin - len;
         rbc[warp * 32 + lane] = make_int2(beg, cl);
         __syncwarp();
+        const int R = (Hw + 31) >> 5;
+        int idle = 0;
+        if (lane == 0 && R >= 2 && R < kJobMaxRounds) idle = *reinterpret_cast<volatile int*>(&n_idle);
+        idle = __shfl_sync(0xffffffffu, idle, 0);
+        if (idle > 0) {
+          // warps of this block whose seeds are all done share these hit rounds
+          if (lane == 0) {
+            // close the job word first (round field 0xFFFF: no claim passes and
+            // every stale CAS fails), then write the job, then open it
+            const int ep = ((job_next[warp] >> 16) + 1) & 0x7FFF;
+            atomicExch(&job_next[warp], (ep << 16) | 0xFFFF);
+            __threadfence_block();
+            job_total[warp] = R;
+            job_hw[warp] = Hw;
+            job_done[warp] = 0;
+            __threadfence_block();
+            atomicExch(&job_next[warp], ep << 16);
+          }
+          __syncwarp();
+          int fin = 0;
+          for (int it = 0; it < kOwnerWaitLimit; ++it) {
+            work_job(warp);
+            if (lane == 0) fin = *reinterpret_cast<volatile int*>(&job_done[warp]) >= R;
+            fin = __shfl_sync(0xffffffffu, fin, 0);
+            if (fin) break;
+            __nanosleep(32);
+          }
+          if (!fin && lane == 0) atomicOr(a.status, kStatTimeout);
+          __threadfence_block();
+          __syncwarp();
+          continue;
+        }
         // the row holding flattened hit h: last lane whose hit prefix is <= h
         auto locate = [&](int h, int& cc, int& pos) {
           int j = 0;
@@ -475,25 +588,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
           }
           cp_async_commit();
           cp_async_wait<1>();
-          if (cc >= 0) {
-            const HitRec hr = unpack_rec(mystage[buf], mystage[buf + 1]);
-            const int* wd = wwin + cc * kWinWords;
-            const float* ps = wprop + cc * kSlotWords;
-            const int kind = wd[0];
-            ++n_chi2;
-            if (hit_in_box(kind, ps[0], ps[1], ps[2], hr, __int_as_float(wd[8]), __int_as_float(wd[9]))) {
-              ++n_full;
-              const PosState q{ps[0], ps[1], ps[2], ps[6 + ci(0, 0)], ps[6 + ci(1, 0)], ps[6 + ci(1, 1)],
-                               ps[6 + ci(2, 0)], ps[6 + ci(2, 1)], ps[6 + ci(2, 2)]};
-              const float chi2 = hit_chi2(kind, q, hr, cut);
-              if (chi2 < cut) {
-                atomicAdd(&cnt[warp * 32 + cc], 1);
-                const uint32_t hloc = (uint32_t)(hr.orig - wd[10]);
-                top_insert(wtop + (cc / GS) * NMAX, N,
-                           child_key(ps[27] + 10.0f - chi2, cc & (GS - 1), hloc < kHoleKey ? hloc : kHoleKey - 1));
-              }
-            }
-          }
+          if (cc >= 0) scan_pair(warp, cc, unpack_rec(mystage[buf], mystage[buf + 1]));
         }
         cp_async_wait<0>();
         __syncwarp();
@@ -630,6 +725,33 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
     }
     __syncwarp();
     fetch(done);
+  }
+  // ---- no seed left for this warp: help the block's other warps with their
+  // wide scans until every warp of the block is done
+  if (lane == 0) {
+    atomicAdd(&n_idle, 1);
+    atomicSub(&n_alive, 1);
+  }
+  for (int it = 0; it < kHelperPollLimit; ++it) {
+    int alive = 0, pending = 0;
+    if (lane == 0) {
+      alive = *reinterpret_cast<volatile int*>(&n_alive);
+      for (int ow = 0; ow < W; ++ow) {
+        const int v = *reinterpret_cast<volatile int*>(&job_next[ow]);
+        const int tot = *reinterpret_cast<volatile int*>(&job_total[ow]);
+        if ((v & 0xFFFF) < tot) pending |= 1 << ow;
+      }
+    }
+    alive = __shfl_sync(0xffffffffu, alive, 0);
+    pending = __shfl_sync(0xffffffffu, pending, 0);
+    if (pending) {
+      for (int ow = 0; ow < W; ++ow)
+        if (pending & (1 << ow)) work_job(ow);
+    } else {
+      if (alive == 0) break;
+      __nanosleep(64);
+    }
+    if (it == kHelperPollLimit - 1 && lane == 0) atomicOr(a.status, kStatTimeout);
   }
   // ---- counters
 #pragma unroll
