@@ -120,9 +120,18 @@ mkf_status mkf_load_geometry(mkf_ctx* ctx, const mkf_layer* layers, int n_layers
   g.n_barrel = (int)bar.size();
   g.n_dpos = (int)dp.size();
   g.n_dneg = (int)dn.size();
-  for (size_t i = 0; i < bar.size(); ++i) g.barrel_order[i] = (int8_t)bar[i].second;
-  for (size_t i = 0; i < dp.size(); ++i) g.dpos_order[i] = (int8_t)dp[i].second;
-  for (size_t i = 0; i < dn.size(); ++i) g.dneg_order[i] = (int8_t)dn[i].second;
+  for (size_t i = 0; i < bar.size(); ++i) {
+    g.barrel_order[i] = (int8_t)bar[i].second;
+    g.barrel_r[i] = bar[i].first;
+  }
+  for (size_t i = 0; i < dp.size(); ++i) {
+    g.dpos_order[i] = (int8_t)dp[i].second;
+    g.dpos_z[i] = dp[i].first;
+  }
+  for (size_t i = 0; i < dn.size(); ++i) {
+    g.dneg_order[i] = (int8_t)dn[i].second;
+    g.dneg_z[i] = dn[i].first;
+  }
   g.bins_per_event = base;
   if (ctx->geom_dev.ensure(sizeof(GeomDev)) != cudaSuccess) return ctx->fail(MKF_ERR_OOM, "geometry buffer");
   MKF_CUDA(cudaMemcpy(ctx->geom_dev.p, &g, sizeof(GeomDev), cudaMemcpyHostToDevice), "geometry upload");

@@ -171,6 +171,20 @@ __device__ __forceinline__ HitRec load_rec(const float4* __restrict__ rec, int p
   return unpack_rec(__ldg(&rec[2 * pos]), __ldg(&rec[2 * pos + 1]));
 }
 
+// first index of the ascending array v[0..n) whose value is above x (n if none,
+// also for x = NaN)
+__device__ __forceinline__ int first_above(const float* v, int n, float x) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (v[mid] > x)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  return lo;
+}
+
 __device__ __forceinline__ int event_of(const int64_t* off, int n_events, int64_t i) {
   int lo = 0, hi = n_events;
   while (hi - lo > 1) {
@@ -366,6 +380,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
     // ---- (1) navigation: next reachable surface outward
     int nl = -1;
     float ns = INFINITY;
+    HelixPt<float> hn;        // the helix at a disk crossing found by the navigation
+    bool have_hn = false;
     float sin_t = 1.f, cos_t = 0.f, cot_t = 0.f, omega = 0.f;
     if (active && step < L) {
       sincosf(p[5], &sin_t, &cos_t);
@@ -373,10 +389,10 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
       omega = ck * p[3];
       float sph, cph;
       sincosf(p[4], &sph, &cph);
-      for (int i = 0; i < G.n_barrel; ++i) {
+      // surfaces already passed form a prefix of each sorted list
+      for (int i = first_above(G.barrel_r, G.n_barrel, rho + kNavEps); i < G.n_barrel; ++i) {
         const int l = G.barrel_order[i];
         const LayerDev& ly = G.L[l];
-        if (!(ly.pos > rho + kNavEps)) continue;
         ++n_nav;
         const float s = cylinder_path(p[0], p[1], cph, sph, omega, ly.pos, +1);
         if (!(s < INFINITY)) break;    // the particle's circle stays inside: larger radii too
@@ -390,14 +406,14 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
       if (cot_t != 0.0f) {
         const int nd = cot_t > 0.f ? G.n_dpos : G.n_dneg;
         const int8_t* ord = cot_t > 0.f ? G.dpos_order : G.dneg_order;
+        const float* dz = cot_t > 0.f ? G.dpos_z : G.dneg_z;
         // a particle leaving the tracking volume is lost: disks count only
         // when crossed before r = r_max
         float s_lim = ns;
         bool exit_known = false;
-        for (int i = 0; i < nd; ++i) {
+        for (int i = first_above(dz, nd, zeta + kNavEps); i < nd; ++i) {
           const int l = ord[i];
           const LayerDev& ly = G.L[l];
-          if (!(fabsf(ly.pos) > zeta + kNavEps)) continue;
           ++n_nav;
           const float s = plane_path(p[2], cot_t, ly.pos, +1);
           if (!(s < s_lim)) break;     // |z| ordered: later disks are farther
@@ -411,6 +427,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
           if (r >= ly.lo && r <= ly.hi) {
             nl = l;
             ns = s;
+            hn = h;
+            have_hn = true;
             break;
           }
         }
@@ -424,7 +442,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
       ++n_steps;
       const LayerDev ly = G.L[nl];
       const int kind = ly.kind;
-      const auto h = helix_at(p[0], p[1], p[2], p[4], cot_t, omega, ns);
+      const auto h = have_hn ? hn : helix_at(p[0], p[1], p[2], p[4], cot_t, omega, ns);
       const auto J = transport_jacobian(kind, p, h, ns, omega, ck, cot_t, sin_t);
       float ms_phi = 0.0f, ms_theta = 0.0f;
       if (ly.x0 > 0.0f) {

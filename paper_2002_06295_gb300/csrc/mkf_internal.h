@@ -36,8 +36,12 @@ struct GeomDev {
   int8_t barrel_order[MKF_MAX_LAYERS];   // barrel ids by increasing r
   int8_t dpos_order[MKF_MAX_LAYERS];     // z > 0 disk ids by increasing z
   int8_t dneg_order[MKF_MAX_LAYERS];     // z < 0 disk ids by increasing |z|
+  float barrel_r[MKF_MAX_LAYERS];        // radius of barrel_order[i]
+  float dpos_z[MKF_MAX_LAYERS];          // |z| of dpos_order[i]
+  float dneg_z[MKF_MAX_LAYERS];          // |z| of dneg_order[i]
   LayerDev L[MKF_MAX_LAYERS];
 };
+static_assert(sizeof(GeomDev) % 16 == 0, "GeomDev is copied to shared memory in 16-byte words");
 
 // Grow-only device buffer owned by the context.
 struct DevBuf {

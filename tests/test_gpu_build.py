@@ -105,6 +105,27 @@ def test_build_config2_sampled_seeds():
     ctx.close()
 
 
+def test_build_stress_event_sampled_seeds():
+    """Stress configuration at full event size: 10000 tracks with pT down to
+    0.3 GeV and |eta| < 2.5 on the 10-cylinder barrel, 50 % noise hits,
+    8 candidates per seed; two events in one launch so that the batched path
+    is exercised; 120 sampled seeds per event are compared with the oracle."""
+    evs = [synth.make_config_event(5, e) for e in range(2)]
+    ctx = make_ctx(evs[0].geom, 128, 32)
+    g = gpu_build(ctx, evs, max_cands=8)
+    rng = np.random.default_rng(11)
+    for i, ev in enumerate(evs):
+        sel = np.sort(rng.choice(ev.n_seeds, 120, replace=False))
+        off = int(g["seed_off"][i])
+        gi = {k: (v[off:off + ev.n_seeds] if isinstance(v, np.ndarray) and v.shape[:1] == (int(g["seed_off"][-1]),)
+                  else v) for k, v in g.items()}
+        hb = int(g["hit_off"][i])
+        gi["hits"] = np.where(gi["hits"] >= 0, gi["hits"] - hb, -1)
+        r = oracle_build([ev], max_cands=8, seeds=sel, dedup=False)
+        _assert_parity(compare(gi, r, sel=sel), max_fragile_frac=0.3)
+    ctx.close()
+
+
 @pytest.mark.parametrize("cfg", [1, 2])
 def test_search_window_is_conservative(cfg):
     """Debug mode evaluates every hit of the layer: no hit with chi2 < cut may
