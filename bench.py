@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--no-secondary", action="store_true", help="skip the C3 batched-vs-plain and C4 fit-gradient lines")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c5"],
                     help="timed workload (c2: the CMS-like event the metric is quoted on)")
+    ap.add_argument("--no-graph", action="store_true", help="time eager launches only (no CUDA-graph replay)")
     return ap.parse_args()
 
 
@@ -246,17 +247,44 @@ def measure_batched(mkf, tune, dev, reps=3):
     tp = tune.autotune_build(ctx, g.table(), g.bz, e0["xyz"], e0["lcov"], e0["lay"], e0["hoff"], e0["sp"], e0["sc"],
                              e0["soff"], max_cands=kw["max_cands"])
     outs = [mkf.alloc_build_outputs(ctx, b.events[i].n_seeds) for i in range(len(evs))]
+
+    def plain():
+        for i, x in enumerate(evs):
+            mkf.mkf_bin_hits(ctx, x["xyz"], x["lcov"], x["lay"], x["hoff"])
+            mkf.mkf_build_tracks(ctx, x["sp"], x["sc"], x["soff"], out=outs[i], **kw)
+
     pt = []
     for r in range(2):
         flush.fill_(float(r))
         a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        for i, x in enumerate(evs):
-            mkf.mkf_bin_hits(ctx, x["xyz"], x["lcov"], x["lay"], x["hoff"])
-            mkf.mkf_build_tracks(ctx, x["sp"], x["sc"], x["soff"], out=outs[i], **kw)
+        plain()
         e.record(stream)
         e.synchronize()
         pt.append(a.elapsed_time(e))
+    mkf.mkf_sync(ctx)
+    # the plain sequence of 256 x (bin + build + dedup) launched as one CUDA graph
+    pg_ms = None
+    try:
+        mkf.mkf_set_timing(ctx, False)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            plain()
+        g.replay()
+        torch.cuda.synchronize()
+        pg = []
+        for r in range(2):
+            flush.fill_(float(r))
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            g.replay()
+            e.record(stream)
+            e.synchronize()
+            pg.append(a.elapsed_time(e))
+        pg_ms = min(pg)
+    except Exception:
+        pg_ms = None
+    mkf.mkf_set_timing(ctx, True)
     mkf.mkf_sync(ctx)
     ctx.close()
     E = b.n_events
@@ -265,6 +293,7 @@ def measure_batched(mkf, tune, dev, reps=3):
                         "%d seeds, %d hits, 4 candidates/seed" % (int(b.seed_off[-1]), int(b.hit_off[-1])),
             "batched_ms": bms, "plain_ms": pms, "batched_events_per_s": E / (bms * 1e-3),
             "plain_events_per_s": E / (pms * 1e-3), "batched_over_plain": pms / bms,
+            "plain_graph_ms": pg_ms, "batched_over_plain_graph": None if pg_ms is None else pg_ms / bms,
             "batched_cand_steps_per_s": steps / (bms * 1e-3),
             "tuned_batched": {k: tb[k] for k in ("n_phi", "n_w", "warps", "lanes")},
             "tuned_plain": {k: tp[k] for k in ("n_phi", "n_w", "warps", "lanes")}}
@@ -445,7 +474,8 @@ def main():
                              dup_frac=spec["dup_frac"], out=out)
         mkf.mkf_fit_tracks(ctx, inp["xyz"], inp["lcov"], inp["layer"], out["hits"], inp["sp"], inp["sc"],
                            ckpt=ckpt, out=fit_out)
-        fwd_done.record(stream)
+        cur = torch.cuda.current_stream()
+        fwd_done.record(cur)
         side.wait_event(fwd_done)
         mkf.mkf_fit_backward(ctx, inp["xyz"], inp["lcov"], inp["layer"], out["hits"], fit_out["par"], out=bwd_out,
                              stream=side)
@@ -456,8 +486,11 @@ def main():
                                            inp["sc"], ckpt, g_chi2=g_chi2, out=adj_out)
             except mkf.MkfError:
                 has_adjoint[0] = False
-        stream.wait_event(bwd_done)
+        cur.wait_event(bwd_done)
 
+    dd_inputs = {k: torch.empty_like(v) for k, v in d.items()}   # device copies of the host inputs (e2e)
+    for k, v in d.items():
+        dd_inputs[k].copy_(v)
     # warm-up
     for _ in range(max(args.warmup, 3) if args.warmup > 0 else 0):
         step(d)
@@ -485,13 +518,55 @@ def main():
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in tev]
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
+    eager_ms = sum(step_ms)
+
+    # the same step captured once as a CUDA graph (the library's calls are
+    # stream-ordered and allocate nothing once warm) and replayed
+    graphs, graph_ms, graph_note = {}, None, None
+    if not args.no_graph:
+        mkf.mkf_set_timing(ctx, False)
+        try:
+            for name, inp in (("dev", d), ("e2e", dd_inputs)):
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g):
+                    step(inp)
+                graphs[name] = g
+            for _ in range(3):
+                graphs["dev"].replay()
+            torch.cuda.synchronize()
+        except Exception as exc:   # capture refused: eager numbers stand
+            graphs, graph_note = {}, "%s: %s" % (type(exc).__name__, str(exc).splitlines()[0][:160])
+        ok = 1 if graphs else 0
+        if dist:   # replay only if every rank captured
+            t = torch.tensor([ok], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MIN)
+            ok = int(t.item())
+        if ok:
+            if dist:
+                dist.barrier()
+            gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(args.steps)]
+            for k in range(args.steps):
+                flush.fill_(float(k))
+                gev[k][0].record(stream)
+                graphs["dev"].replay()
+                gev[k][1].record(stream)
+            torch.cuda.synchronize()
+            if dist:
+                dist.barrier()
+            graph_ms = sum(a.elapsed_time(b) for a, b in gev)
+        else:
+            graphs = {}
+        mkf.mkf_set_timing(ctx, True)
+        mkf.mkf_sync(ctx)
+    clk = clocks.stop()
+    if dist:   # every rank takes the slowest rank's times and the same launch mode
+        t = torch.tensor([eager_ms, graph_ms if graph_ms is not None else float("inf")], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        eager_ms, graph_ms = float(t[0].item()), (float(t[1].item()) if t[1].item() < float("inf") else None)
+    use_graph = graph_ms is not None and graph_ms < eager_ms
+    total_ms = graph_ms if use_graph else eager_ms
 
     # end to end through the API with host buffers: H2D inputs, path, D2H results
     h2d = sum(v.numel() * v.element_size() for v in host.values())
@@ -501,7 +576,7 @@ def main():
                     chi2=torch.empty_like(fit_out["chi2"], device="cpu").pin_memory())
     d2h = sum(v.numel() * v.element_size() for v in res_host.values())
     e2e_ms = []
-    dd = {k: torch.empty_like(v) for k, v in d.items()}
+    dd = dd_inputs
     for k in range(args.steps):
         flush.fill_(float(k))
         torch.cuda.synchronize()
@@ -509,7 +584,10 @@ def main():
         a.record(stream)
         for kk, v in host.items():
             dd[kk].copy_(v, non_blocking=True)
-        step(dd)
+        if use_graph:
+            graphs["e2e"].replay()
+        else:
+            step(dd)
         res_host["hits"].copy_(out["hits"], non_blocking=True)
         res_host["par"].copy_(fit_out["par"], non_blocking=True)
         res_host["flags"].copy_(out["flags"], non_blocking=True)
@@ -537,7 +615,8 @@ def main():
     props = torch.cuda.get_device_properties(dev)
     max_mhz = clk.get("sm_max_mhz") or measured_peaks().get("sm_max_mhz", 2070.0)
     peak = props.multi_processor_count * FP32_LANES * 2 * max_mhz * 1e6 / 1e12
-    launches_per_step = 6 + 1 + 3 + 1 + (1 if has_adjoint[0] else 0) + 1
+    # binning 5 (keys, 3-pass scan, scatter), building 1, dedup 3, fit 1, adjoint 1, inward fit 1
+    launches_per_step = 5 + 1 + 3 + 1 + (1 if has_adjoint[0] else 0) + 1
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -546,6 +625,7 @@ def main():
                    "hits": n_hits,
                    "surfaces": L, "max_cands": spec["max_cands"], "l2": "flushed (256 MB write) between timed steps",
                    "adjoint_in_step": has_adjoint[0],
+                   "launch": "cuda_graph" if use_graph else "eager",
                    "tuned": {k: tuned[k] for k in ("n_phi", "n_w", "warps", "lanes")}},
         "events_per_s": world * len(evs) * args.steps / (total_ms * 1e-3),
         "fit_tracks_per_s": world * S * args.steps / (total_ms * 1e-3),
@@ -563,6 +643,9 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": statistics.mean(e2e_ms)},
         "gpu_launches": launches_per_step * args.steps,
+        "launch_ms_per_step": {"eager": eager_ms / args.steps,
+                               "cuda_graph": None if graph_ms is None else graph_ms / args.steps,
+                               "graph_note": graph_note},
         "secondary": secondary,
         "clocks": clk,
     }

@@ -122,7 +122,9 @@ def test_build_stress_event_sampled_seeds():
         hb = int(g["hit_off"][i])
         gi["hits"] = np.where(gi["hits"] >= 0, gi["hits"] - hb, -1)
         r = oracle_build([ev], max_cands=8, seeds=sel, dedup=False)
-        _assert_parity(compare(gi, r, sel=sel), max_fragile_frac=0.3)
+        # forward low-pT tracks with few hits carry correlations near 1 that
+        # FP32 storage keeps to a few 1e-4 (as on the CMS-like geometry)
+        _assert_parity(compare(gi, r, sel=sel), max_fragile_frac=0.3, cov_frac=0.8, cov_cap=2e-3)
     ctx.close()
 
 
