@@ -4,9 +4,9 @@
 //
 // The outward fit runs in FP32.  The inward fit starts from a prior 100 times
 // wider than the seed's, so its first updates shrink variances by factors up
-// to 1e5; FP32 cannot carry those cancellations to 1e-4, so the first
-// kInwardFp64Updates updates run in FP64.  By then the state is constrained
-// and the rest of the inward fit runs in FP32 like the outward fit.
+// to 1e5, and on mixed barrel/disk tracks the state keeps correlations close
+// to 1 for many hits: FP32 cannot carry its covariance to 1e-4, so the inward
+// fit runs in FP64.
 #include "mkf_device.cuh"
 #include "mkf_fit_common.cuh"
 #include "mkf_internal.h"
@@ -60,10 +60,9 @@ __global__ void k_fit(const GeomDev* __restrict__ g, const float* __restrict__ x
   if (out_ok) out_ok[t] = ok;
 }
 
-constexpr int kInwardFp64Updates = 4;
-
 // Inward fit: covariance reset to 100 x the seed-style diagonal, update with
-// the outermost hit in place, then propagate inward hit by hit.
+// the outermost hit in place, then propagate inward hit by hit (FP64, plain
+// covariance update).
 __global__ void k_fit_inward(const GeomDev* __restrict__ g, const float* __restrict__ xyz,
                              const float* __restrict__ lcov, const int* __restrict__ layer, int64_t H,
                              const int* __restrict__ hits, int K, const float* __restrict__ init_par, int64_t NT,
@@ -73,58 +72,37 @@ __global__ void k_fit_inward(const GeomDev* __restrict__ g, const float* __restr
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= NT) return;
   const int* row = hits + t * K;
-  double pd[6], Cd[21];
+  double p[6], C[21];
 #pragma unroll
-  for (int k = 0; k < 6; ++k) pd[k] = double(init_par[k * NT + t]);
+  for (int k = 0; k < 6; ++k) p[k] = double(init_par[k * NT + t]);
 #pragma unroll
-  for (int k = 0; k < 21; ++k) Cd[k] = 0.0;
-  Cd[ci(0, 0)] = Cd[ci(1, 1)] = Cd[ci(2, 2)] = 1.0;
-  Cd[ci(3, 3)] = 100.0 * (0.05 * pd[3]) * (0.05 * pd[3]);
-  Cd[ci(4, 4)] = Cd[ci(5, 5)] = 0.25;
+  for (int k = 0; k < 21; ++k) C[k] = 0.0;
+  C[ci(0, 0)] = C[ci(1, 1)] = C[ci(2, 2)] = 1.0;
+  C[ci(3, 3)] = 100.0 * (0.05 * p[3]) * (0.05 * p[3]);
+  C[ci(4, 4)] = C[ci(5, 5)] = 0.25;
   int last = -1;
   for (int k = K - 1; k >= 0; --k)
     if (row[k] >= 0) {
       last = k;
       break;
     }
-  double chi2d = 0.0;
-  int ok = 1, k = last, done = 0;
-  {
-    const double ck = double(g->c_kappa);
-    FitHit<double> f;
-    for (; k >= 0 && done < kInwardFp64Updates; --k) {
-      if (!load_fit_hit(g, xyz, lcov, layer, H, row[k], align, x0, f)) continue;
-      if (k != last && !step_to(f, pd, Cd, ck, -1)) {
-        ok = 0;
-        break;
-      }
-      chi2d += kf_update(f.kind, pd, Cd, f.m);
-      ++done;
+  double chi2 = 0.0;
+  int ok = 1;
+  const double ck = double(g->c_kappa);
+  FitHit<double> f;
+  for (int k = last; k >= 0; --k) {
+    if (!load_fit_hit(g, xyz, lcov, layer, H, row[k], align, x0, f)) continue;
+    if (k != last && !step_to(f, p, C, ck, -1)) {
+      ok = 0;
+      break;
     }
-  }
-  float p[6], C[21];
-#pragma unroll
-  for (int i = 0; i < 6; ++i) p[i] = float(pd[i]);
-#pragma unroll
-  for (int i = 0; i < 21; ++i) C[i] = float(Cd[i]);
-  float chi2 = 0.0f;
-  if (ok) {
-    const float ck = g->c_kappa;
-    FitHit<float> f;
-    for (; k >= 0; --k) {
-      if (!load_fit_hit(g, xyz, lcov, layer, H, row[k], align, x0, f)) continue;
-      if (k != last && !step_to(f, p, C, ck, -1)) {
-        ok = 0;
-        break;
-      }
-      chi2 += kf_update(f.kind, p, C, f.m);
-    }
+    chi2 += kf_update<double, false>(f.kind, p, C, f.m);
   }
 #pragma unroll
-  for (int i = 0; i < 6; ++i) out_par[i * NT + t] = p[i];
+  for (int i = 0; i < 6; ++i) out_par[i * NT + t] = float(p[i]);
 #pragma unroll
-  for (int i = 0; i < 21; ++i) out_cov[i * NT + t] = C[i];
-  out_chi2[t] = float(chi2d + double(chi2));
+  for (int i = 0; i < 21; ++i) out_cov[i * NT + t] = float(C[i]);
+  out_chi2[t] = float(chi2);
   if (out_ok) out_ok[t] = ok;
 }
 

@@ -315,8 +315,12 @@ __device__ __forceinline__ PosState pos_state(const float p[6], const float C[21
 }
 
 // Kalman update with the hit: B = C H^T, R = V + H B, K = B R^-1,
-// p += K r, C -= B R^-1 B^T.  Returns the predicted chi2.
-template <class T> __device__ __forceinline__ T kf_update(int kind, T p[6], T C[21], const Meas<T>& h) {
+// p += K r, C -= B R^-1 B^T.  Returns the predicted chi2.  JOSEPH selects the
+// Joseph form of the covariance update (needed in FP32, see below); the plain
+// form C - B W B^T is used in FP64, where it keeps full precision at less than
+// half the operations.
+template <class T, bool JOSEPH = true>
+__device__ __forceinline__ T kf_update(int kind, T p[6], T C[21], const Meas<T>& h) {
   T B[6][2];
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
@@ -339,6 +343,14 @@ template <class T> __device__ __forceinline__ T kf_update(int kind, T p[6], T C[
     p[i] = mfma(K[i][0], ra, mfma(K[i][1], rb, p[i]));
   }
   p[4] = wrap_phi(p[4]);
+  if (!JOSEPH) {
+    // C' = C - B W B^T = C - K B^T
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = 0; j <= i; ++j) C[ci(i, j)] = mfma(-K[i][0], B[j][0], mfma(-K[i][1], B[j][1], C[ci(i, j)]));
+    return chi2;
+  }
   // Covariance in Joseph form, C' = (I - K H) C (I - K H)^T + K V K^T: a sum of
   // positive terms whose rounding does not grow when the hit shrinks a variance
   // by orders of magnitude (the plain C - B W B^T loses those digits in FP32).

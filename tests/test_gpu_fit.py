@@ -111,3 +111,41 @@ def test_fit_cmslike_mixed_surfaces():
     print("cms-like fit: cov err max", ce.max(), "fraction within 1e-4", (ce.max(1) < COV_RTOL).mean())
     assert cov_ok(ce, frac=0.9, cap=2e-3)
     ctx.close()
+
+
+def test_backward_fit_cmslike_mixed_surfaces():
+    """Inward fit over barrel and disk hits (CMS-like geometry) from the
+    oracle's outward result: the 100x prior and the correlations near 1 that
+    mixed barrel/disk tracks keep are what the inward fit's precision must
+    carry."""
+    import oracle
+    import paper_2002_06295_gb300 as mkf
+    g = synth.geometry_cmslike()
+    rng = np.random.default_rng(14)
+    ev = synth.simulate_event(g, 1500, rng, pt_range=(0.8, 20.0), pt_log=True, eta_max=2.4)
+    keep = (ev.true_hits >= 0).sum(1) >= 6
+    hits, sp, sc = ev.true_hits[keep], ev.seed_par[keep], ev.seed_cov[keep]
+    # inputs quantised to float32 so that both sides see the same numbers: a
+    # track with few hits and a short lever arm turns the rounding of its hit
+    # positions (~1e-7 relative) into ~1e-3 of its own curvature
+    q = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    ev.hit_xyz, ev.hit_lcov = q(ev.hit_xyz), q(ev.hit_lcov)
+    geo = oracle.Geo.of(g)
+    fpar, fcov, _, fok = oracle.fit(geo, ev.hit_xyz, ev.hit_lcov, ev.hit_layer, hits, q(sp), q(sc))
+    fpar = q(fpar)
+    bpar, bcov, _, bok = oracle.fit(geo, ev.hit_xyz, ev.hit_lcov, ev.hit_layer, hits, fpar, fcov, direction=-1)
+    dev = torch.device("cuda", 0)
+    ctx = make_ctx(g)
+    o = mkf.mkf_fit_backward(ctx, f32(ev.hit_xyz.T, dev), f32(ev.hit_lcov.T, dev), i32(ev.hit_layer, dev),
+                             i32(hits, dev), f32(fpar.T, dev))
+    mkf.mkf_sync(ctx)
+    gp = o["par"].cpu().numpy().T.astype(np.float64)
+    gc = o["cov"].cpu().numpy().T.astype(np.float64)
+    good = fok.astype(bool) & bok.astype(bool) & (o["ok"].cpu().numpy() == 1)
+    assert good.mean() > 0.99
+    pe, ce = par_rel_err(gp[good], bpar[good]), cov_rel_err(gc[good], bcov[good])
+    print("cms-like backward fit: par err per parameter", pe.max(0), "cov err max", ce.max(),
+          "fraction within 1e-4", (ce.max(1) < COV_RTOL).mean())
+    assert pe.max() < PAR_RTOL
+    assert cov_ok(ce, frac=0.9, cap=2e-3)
+    ctx.close()
