@@ -384,11 +384,11 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
     bool have_hn = false;
     float sin_t = 1.f, cos_t = 0.f, cot_t = 0.f, omega = 0.f;
     if (active && step < L) {
-      sincosf(p[5], &sin_t, &cos_t);
+      msincos(p[5], &sin_t, &cos_t);
       cot_t = cos_t / sin_t;
       omega = ck * p[3];
       float sph, cph;
-      sincosf(p[4], &sph, &cph);
+      msincos(p[4], &sph, &cph);
       // surfaces already passed form a prefix of each sorted list
       for (int i = first_above(G.barrel_r, G.n_barrel, rho + kNavEps); i < G.n_barrel; ++i) {
         const int l = G.barrel_order[i];

@@ -32,13 +32,26 @@ __device__ __forceinline__ float vv(float x) { return x; }
 __device__ __forceinline__ double vv(double x) { return x; }
 __device__ __forceinline__ float mfma(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double mfma(double a, double b, double c) { return fma(a, b, c); }
-__device__ __forceinline__ void msincos(float x, float* s, float* c) { sincosf(x, s, c); }
+// FP32 sincos and atan are called from several places of the building
+// kernel; one out-of-line copy each (with their rarely taken large-argument
+// paths) keeps the kernel's code small enough for the instruction caches.
+static __device__ __noinline__ float2 msincos_f(float x) {
+  float2 r;
+  sincosf(x, &r.x, &r.y);
+  return r;
+}
+__device__ __forceinline__ void msincos(float x, float* s, float* c) {
+  const float2 r = msincos_f(x);
+  *s = r.x;
+  *c = r.y;
+}
 __device__ __forceinline__ void msincos(double x, double* s, double* c) { sincos(x, s, c); }
 __device__ __forceinline__ float msqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double msqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float mrsqrt(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double mrsqrt(double x) { return rsqrt(x); }
-__device__ __forceinline__ float matan(float x) { return atanf(x); }
+static __device__ __noinline__ float matan_f(float x) { return atanf(x); }
+__device__ __forceinline__ float matan(float x) { return matan_f(x); }
 __device__ __forceinline__ double matan(double x) { return atan(x); }
 __device__ __forceinline__ float mlog(float x) { return logf(x); }
 __device__ __forceinline__ double mlog(double x) { return log(x); }
@@ -68,7 +81,9 @@ template <class T> __device__ __forceinline__ void sinc_and_deriv(T u, T su, T c
 
 // Convert a root sigma = tan(omega s / 2) / omega of the crossing equation
 // into the transverse path s in the requested direction (dir > 0: s > 0,
-// smallest; dir < 0: s < 0, smallest |s|).  atan(t)/t -> 1 keeps omega -> 0 exact.
+// smallest; dir < 0: s < 0, smallest |s|).  atan(t)/t -> 1 keeps omega -> 0
+// exact.  s has the sign of sigma and grows with it; a root on the wrong side
+// is moved one turn on, beyond every root on the right side.
 template <class T> __device__ __forceinline__ T sigma_to_path(T sig, T omega, int dir) {
   T t = omega * sig;
   T s;
@@ -103,10 +118,22 @@ __device__ __forceinline__ T cylinder_path(T x0, T y0, T cph, T sph, T omega, T 
   T disc = mfma(a, a, -A * D);
   if (!(vv(disc) >= 0)) return T(dir > 0 ? INFINITY : -INFINITY);
   T q = T(-0.5) * (a + mcopysign(msqrt(disc), a));
-  T s1 = sigma_to_path(q / A, omega, dir);
-  T s2 = sigma_to_path(T(0.25) * D / q, omega, dir);
-  if (dir > 0) return vv(s2) < vv(s1) ? s2 : s1;
-  return vv(s2) > vv(s1) ? s2 : s1;
+  const T g1 = q / A, g2 = T(0.25) * D / q;
+  // The root giving the shortest path in the requested direction, chosen on
+  // sigma and then converted alone: s grows with sigma and has its sign, and a
+  // root on the wrong side is moved by one turn, which keeps the order among
+  // roots on the same side.  So, both on the same side: dir > 0 takes the
+  // smaller sigma, dir < 0 the larger; otherwise the root on the requested side.
+  const auto v1 = vv(g1), v2 = vv(g2);
+  bool take2;
+  if (dir > 0) {
+    const bool p1 = v1 > 0, p2 = v2 > 0;
+    take2 = p1 == p2 ? v2 < v1 : p2;
+  } else {
+    const bool n1 = v1 < 0, n2 = v2 < 0;
+    take2 = n1 == n2 ? v2 > v1 : n2;
+  }
+  return sigma_to_path(take2 ? g2 : g1, omega, dir);
 }
 
 // Transverse path to the plane z = Z (+-inf when parallel or behind).
