@@ -243,10 +243,10 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
   const unsigned gfull = GS == 32 ? 0xffffffffu : ((1u << GS) - 1u);
   const unsigned gmask = gfull << gbase;
 
-  float4* stage = reinterpret_cast<float4*>(smem + sizeof(GeomDev));               // [W][32][2 buffers][2]
+  float4* stage = reinterpret_cast<float4*>(smem + sizeof(GeomDev));               // [W][4 slots][32]
   float* prop = reinterpret_cast<float*>(stage + W * 32 * 4);                       // [W][32][kSlotWords]
   int* win = reinterpret_cast<int*>(prop + W * 32 * kSlotWords);                   // [W][32][kWinWords]
-  int* cnt = win + W * 32 * kWinWords;                                              // [W][32]
+  int* cnt = win + W * 32 * kWinWords;                                              // [W][32] has a child
   int* rowp = cnt + W * 32;                                                         // [W][32]
   int* rpre = rowp + W * 32;                                                        // [W][32]
   int2* rbc = reinterpret_cast<int2*>(rpre + W * 32);                               // [W][32]
@@ -254,7 +254,9 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
   float* bests = reinterpret_cast<float*>(top + W * NG * NMAX);                     // [W][NG][32]
   uint32_t* hist = reinterpret_cast<uint32_t*>(bests + W * NG * 32);                // [W][NG][L][NMAX]
   float* myprop = prop + (warp * 32 + lane) * kSlotWords;
-  float4* mystage = stage + (warp * 32 + lane) * 4;
+  // staging slot k of this lane: slot-major, so that the lanes' 16-byte
+  // accesses to one slot are consecutive (no bank conflicts)
+  float4* mystage = stage + warp * 32 * 4 + lane;
   float* gprop = prop + (warp * 32 + gbase) * kSlotWords;
   int* mywin = win + (warp * 32 + lane) * kWinWords;
   int* gwin = win + (warp * 32 + gbase) * kWinWords;
@@ -326,7 +328,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
                        ps[6 + ci(2, 0)], ps[6 + ci(2, 1)], ps[6 + ci(2, 2)]};
       const float chi2 = hit_chi2(kind, q, hr, cut);
       if (chi2 < cut) {
-        atomicAdd(&cnt[ow * 32 + cc], 1);
+        cnt[ow * 32 + cc] = 1;   // the candidate has a child (only "none" is tested)
         const uint32_t hloc = (uint32_t)(hr.orig - wd[10]);
         top_insert(top + (ow * NG + cc / GS) * NMAX, N,
                    child_key(ps[27] + 10.0f - chi2, cc & (GS - 1), hloc < kHoleKey ? hloc : kHoleKey - 1));
@@ -593,7 +595,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
         if (lane < Hw) {
           locate(lane, cc_n, pos_n);
           cp_async16(mystage, a.rec + 2 * pos_n);
-          cp_async16(mystage + 1, a.rec + 2 * pos_n + 1);
+          cp_async16(mystage + 32, a.rec + 2 * pos_n + 1);
         }
         cp_async_commit();
         for (int h0 = 0, buf = 0; h0 < Hw; h0 += 32, buf ^= 2) {
@@ -601,12 +603,12 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
           cc_n = -1;
           if (h0 + 32 + lane < Hw) {
             locate(h0 + 32 + lane, cc_n, pos_n);
-            cp_async16(mystage + (buf ^ 2), a.rec + 2 * pos_n);
-            cp_async16(mystage + (buf ^ 2) + 1, a.rec + 2 * pos_n + 1);
+            cp_async16(mystage + 32 * (buf ^ 2), a.rec + 2 * pos_n);
+            cp_async16(mystage + 32 * ((buf ^ 2) + 1), a.rec + 2 * pos_n + 1);
           }
           cp_async_commit();
           cp_async_wait<1>();
-          if (cc >= 0) scan_pair(warp, cc, unpack_rec(mystage[buf], mystage[buf + 1]));
+          if (cc >= 0) scan_pair(warp, cc, unpack_rec(mystage[32 * buf], mystage[32 * (buf + 1)]));
         }
         cp_async_wait<0>();
         __syncwarp();

@@ -23,8 +23,9 @@ struct LayerDev {
   int nphi, nw, bin_base;
   float phi_scale;   // nphi / (2 pi)
   float w_scale;     // nw / (hi - lo)
-  float pad0, pad1;
+  float pad0;        // 11 words: an odd stride keeps lanes reading different layers off one bank
 };
+static_assert(sizeof(LayerDev) == 44, "LayerDev layout");
 
 struct GeomDev {
   int n_layers;
