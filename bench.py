@@ -421,9 +421,15 @@ def main():
         per = args.cpu_sample_seeds or 5000
         u, dt = oracle_step(pool, cores, per, 0)
         pool.close()
+        pool1 = oracle_pool(1)   # the same oracle on one core, on a smaller sample
+        per1 = max(1, per // 16)
+        u1, dt1 = oracle_step(pool1, 1, per1, 0)
+        pool1.close()
         cpu = {"value": u / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": "%d of the 5000 seeds of the C2 event (building only, FP64, brute-force hit search), "
-                         "one process per core, %.1f s wall" % (per, dt)}
+                         "one process per core, %.1f s wall" % (per, dt),
+               "one_core": {"value": u1 / dt1, "unit": UNIT, "cores": 1,
+                            "sample": "%d seeds of the same event, %.1f s" % (per1, dt1)}}
 
     dev = torch.device("cuda", local)
     cfg_id = {"c2": 2, "c3": 3, "c5": 5}[args.workload]
@@ -614,6 +620,7 @@ def main():
     achieved = alg_flops / (b_ms * 1e-3) / 1e12
     props = torch.cuda.get_device_properties(dev)
     max_mhz = clk.get("sm_max_mhz") or measured_peaks().get("sm_max_mhz", 2070.0)
+    fma_peak = mkf.mkf_measure_fp32_peak(ctx)   # confirms the derived peak on this device
     peak = props.multi_processor_count * FP32_LANES * 2 * max_mhz * 1e6 / 1e12
     # binning 5 (keys, 3-pass scan, scatter), building 1, dedup 3, fit 1, adjoint 1, inward fit 1
     launches_per_step = 5 + 1 + 3 + 1 + (1 if has_adjoint[0] else 0) + 1
@@ -638,6 +645,7 @@ def main():
                      "traffic": profiled_traffic(args.workload),
                      "peak_basis": "FP32: %d SMs x %d lanes x 2 x %.0f MHz" % (props.multi_processor_count,
                                                                                FP32_LANES, max_mhz),
+                     "peak_fma_probe_tflops": fma_peak,
                      "algorithmic_flops_per_launch": alg_flops},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

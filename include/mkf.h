@@ -100,6 +100,20 @@ mkf_status mkf_load_geometry(mkf_ctx* ctx, const mkf_layer* layers, int n_layers
 mkf_status mkf_bin_hits(mkf_ctx* ctx, const float* xyz, const float* lcov, const int* layer, int64_t n_hits,
                         const int64_t* ev_hit_off, int n_events, void* stream);
 
+/* Iterative tracking (Sec. 3: hits used by the tracks of an iteration are
+ * masked for the following iterations).  mkf_bin_hits_masked bins like
+ * mkf_bin_hits but leaves out every hit h with mask[h] != 0 (DEVICE uint8 [H],
+ * NULL = none): no later mkf_build_tracks can return it, and it does not enter
+ * the window bounds; the bin offsets then cover only the hits left in.
+ * mkf_used_hits sets mask[h] = 1 (DEVICE uint8 [n_hits], not cleared first)
+ * for every hit of the tracks whose flag is MKF_TRK_KEPT (hits [T][L] caller
+ * hit ids, -1 = none; flags [T] as written by mkf_build_tracks); an id outside
+ * 0..n_hits-1 is skipped and reported as MKF_ERR_ARG by mkf_sync. */
+mkf_status mkf_bin_hits_masked(mkf_ctx* ctx, const float* xyz, const float* lcov, const int* layer, int64_t n_hits,
+                               const int64_t* ev_hit_off, int n_events, const uint8_t* mask, void* stream);
+mkf_status mkf_used_hits(mkf_ctx* ctx, const int* hits, int L, const int* flags, int64_t n_tracks, int64_t n_hits,
+                         uint8_t* mask, void* stream);
+
 /* Read back the binning (for inspection and tests): perm [H] original id of
  * each sorted position, bin_off [n_bins_total+1] first sorted position of each
  * (event, layer, bin), n_bins_total = n_events * sum_l(n_phi_l * n_w_l).
@@ -177,6 +191,13 @@ mkf_status mkf_get_stats(mkf_ctx* ctx, int64_t* out, int n, void* stream);
  * since timing was switched on reads as -1.  HOST output of n <= 8 floats. */
 mkf_status mkf_set_timing(mkf_ctx* ctx, int on);
 mkf_status mkf_get_timings(mkf_ctx* ctx, float* ms, int n, void* stream);
+
+/* FP32 FMA throughput of the context's device in TFLOP/s (HOST output),
+ * measured with a kernel of independent FMA chains over every SM (best of two
+ * timed launches after a warm-up; synchronises `stream`).  The paper has no
+ * counterpart: it confirms the FP32 peak against which the building kernel's
+ * roofline fraction is stated. */
+mkf_status mkf_measure_fp32_peak(mkf_ctx* ctx, float* out_tflops, void* stream);
 
 /* Duplicate removal alone on given tracks (same rule as in mkf_build_tracks):
  *   hits [S][L] hit ids (-1 none), score [S], nhits [S], ev_seed_off [E+1]

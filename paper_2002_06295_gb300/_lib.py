@@ -21,6 +21,8 @@ SIGNATURES = {
     "mkf_sync": (i32, [P, P]),
     "mkf_load_geometry": (i32, [P, P, i32, f32]),
     "mkf_bin_hits": (i32, [P, P, P, P, i64, P, i32, P]),
+    "mkf_bin_hits_masked": (i32, [P, P, P, P, i64, P, i32, P, P]),
+    "mkf_used_hits": (i32, [P, P, i32, P, i64, i64, P, P]),
     "mkf_get_binning": (i32, [P, P, P, ctypes.POINTER(i64), P]),
     "mkf_build_tracks": (i32, [P, P, P, P, i64, f32, i32, i32, i32, f32, P, P, P, P, P, P, P, P, P]),
     "mkf_set_debug": (i32, [P, i32]),
@@ -29,6 +31,7 @@ SIGNATURES = {
     "mkf_get_stats": (i32, [P, P, i32, P]),
     "mkf_set_timing": (i32, [P, i32]),
     "mkf_get_timings": (i32, [P, P, i32, P]),
+    "mkf_measure_fp32_peak": (i32, [P, P, P]),
     "mkf_dedup_tracks": (i32, [P, P, i32, P, P, P, i32, i64, i64, i32, f32, P, P]),
     "mkf_dedup_tracks_noalloc": (i32, [P, i32, P, P, P, i32, i64, i64, i32, f32, P, P, P]),
     "mkf_fit_tracks": (i32, [P, P, P, P, i64, P, i32, P, P, i64, P, P, P, P, P, P, P, P]),

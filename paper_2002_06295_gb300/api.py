@@ -103,6 +103,27 @@ def mkf_bin_hits(ctx, xyz, lcov, layer, ev_hit_off, stream=None):
     ctx.n_events = E
 
 
+def mkf_bin_hits_masked(ctx, xyz, lcov, layer, ev_hit_off, mask=None, stream=None):
+    """mkf_bin_hits leaving out the hits with mask[h] != 0 (uint8 tensor [H])."""
+    H = int(layer.shape[0])
+    E = int(ev_hit_off.shape[0]) - 1
+    ctx._check(ctx.lib.mkf_bin_hits_masked(ctx.h, _ptr(xyz, torch.float32, "xyz"), _ptr(lcov, torch.float32, "lcov"),
+                                           _ptr(layer, torch.int32, "layer"), H,
+                                           _ptr(ev_hit_off, torch.int64, "ev_hit_off"), E,
+                                           _ptr(mask, torch.uint8, "mask"), _stream(stream)), "mkf_bin_hits_masked")
+    ctx.n_hits = H
+    ctx.n_events = E
+
+
+def mkf_used_hits(ctx, hits, flags, n_hits, mask=None, stream=None):
+    """uint8 mask [n_hits] with 1 at every hit of a kept track (added to `mask` if given)."""
+    T, L = int(hits.shape[0]), int(hits.shape[1])
+    m = mask if mask is not None else torch.zeros(int(n_hits), dtype=torch.uint8, device=hits.device)
+    ctx._check(ctx.lib.mkf_used_hits(ctx.h, _ptr(hits, torch.int32, "hits"), L, _ptr(flags, torch.int32, "flags"), T,
+                                     int(n_hits), _ptr(m, torch.uint8, "mask"), _stream(stream)), "mkf_used_hits")
+    return m
+
+
 def mkf_get_binning(ctx, stream=None):
     n = ctypes.c_int64()
     ctx._check(ctx.lib.mkf_get_binning(ctx.h, None, None, ctypes.byref(n), _stream(stream)), "mkf_get_binning")
@@ -175,6 +196,13 @@ def mkf_get_timings(ctx, stream=None):
     ctx._check(ctx.lib.mkf_get_timings(ctx.h, ctypes.cast(buf, ctypes.c_void_p), 6, _stream(stream)),
                "mkf_get_timings")
     return {k: float(buf[i]) for i, k in enumerate(TIMER_NAMES)}
+
+
+def mkf_measure_fp32_peak(ctx, stream=None):
+    v = (ctypes.c_float * 1)()
+    ctx._check(ctx.lib.mkf_measure_fp32_peak(ctx.h, ctypes.cast(v, ctypes.c_void_p), _stream(stream)),
+               "mkf_measure_fp32_peak")
+    return float(v[0])
 
 
 def mkf_dedup_tracks(ctx, hits, score, nhits, ev_seed_off, n_hits_total, min_hits=4, dup_frac=0.5, out_flags=None,

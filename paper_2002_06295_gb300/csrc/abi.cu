@@ -54,10 +54,11 @@ void mkf_destroy(mkf_ctx* ctx) {
       cudaEventDestroy(ctx->t_beg[i]);
       cudaEventDestroy(ctx->t_end[i]);
     }
-  DevBuf* bufs[] = {&ctx->geom_dev, &ctx->rec, &ctx->perm, &ctx->bin_off, &ctx->bin_cnt, &ctx->keys,
-                    &ctx->ranks, &ctx->vmax, &ctx->ev_hit_off, &ctx->scan_part, &ctx->seed_ctr, &ctx->stats,
-                    &ctx->status, &ctx->dd_head, &ctx->dd_next, &ctx->dd_beat, &ctx->dd_nbeat, &ctx->dd_state,
-                    &ctx->track_hits};
+  DevBuf* bufs[] = {&ctx->geom_dev, &ctx->rec,     &ctx->rec_orig,  &ctx->perm,     &ctx->bin_off,
+                    &ctx->bin_cnt,  &ctx->keys,    &ctx->ranks,     &ctx->vmax,     &ctx->ev_hit_off,
+                    &ctx->scan_part, &ctx->seed_ctr, &ctx->stats,    &ctx->status,   &ctx->dd_head,
+                    &ctx->dd_next,  &ctx->dd_beat, &ctx->dd_nbeat,  &ctx->dd_state, &ctx->track_hits,
+                    &ctx->probe_buf};
   for (DevBuf* b : bufs) b->release();
   delete ctx;
 }
@@ -143,6 +144,23 @@ mkf_status mkf_load_geometry(mkf_ctx* ctx, const mkf_layer* layers, int n_layers
 
 mkf_status mkf_bin_hits(mkf_ctx* ctx, const float* xyz, const float* lcov, const int* layer, int64_t n_hits,
                         const int64_t* ev_hit_off, int n_events, void* stream) {
+  return mkf_bin_hits_masked(ctx, xyz, lcov, layer, n_hits, ev_hit_off, n_events, nullptr, stream);
+}
+
+mkf_status mkf_used_hits(mkf_ctx* ctx, const int* hits, int L, const int* flags, int64_t n_tracks, int64_t n_hits,
+                         uint8_t* mask, void* stream) {
+  if (check_ctx(ctx)) return MKF_ERR_ARG;
+  if (L < 1 || L > MKF_MAX_LAYERS || n_tracks < 0 || n_hits < 0 || n_tracks > (int64_t)INT32_MAX / MKF_MAX_LAYERS)
+    return ctx->fail(MKF_ERR_ARG, "bad sizes");
+  if (n_tracks > 0 && (!hits || !flags || !mask)) return ctx->fail(MKF_ERR_ARG, "null array");
+  if ((ctx->status.ensure(sizeof(int))) != cudaSuccess) return ctx->fail(MKF_ERR_OOM, "status word");
+  cudaError_t e = launch_used_hits(ctx, hits, flags, n_tracks, L, n_hits, mask, (cudaStream_t)stream);
+  if (e != cudaSuccess) return ctx->cuda_fail(e, "used_hits");
+  return MKF_OK;
+}
+
+mkf_status mkf_bin_hits_masked(mkf_ctx* ctx, const float* xyz, const float* lcov, const int* layer, int64_t n_hits,
+                               const int64_t* ev_hit_off, int n_events, const uint8_t* mask, void* stream) {
   if (check_ctx(ctx)) return MKF_ERR_ARG;
   if (!ctx->have_geom) return ctx->fail(MKF_ERR_STATE, "no geometry loaded");
   if (n_hits < 0 || n_hits > (int64_t)INT32_MAX - 1 || n_events < 1 || !ev_hit_off)
@@ -150,7 +168,7 @@ mkf_status mkf_bin_hits(mkf_ctx* ctx, const float* xyz, const float* lcov, const
   if (n_hits > 0 && (!xyz || !lcov || !layer)) return ctx->fail(MKF_ERR_ARG, "null hit array");
   if ((int64_t)n_events * ctx->geom.bins_per_event >= (int64_t)INT32_MAX)
     return ctx->fail(MKF_ERR_ARG, "too many bins for int32 offsets");
-  cudaError_t e = launch_bin_hits(ctx, xyz, lcov, layer, n_hits, ev_hit_off, n_events, (cudaStream_t)stream);
+  cudaError_t e = launch_bin_hits(ctx, xyz, lcov, layer, n_hits, ev_hit_off, n_events, mask, (cudaStream_t)stream);
   if (e == cudaErrorMemoryAllocation) return ctx->fail(MKF_ERR_OOM, "binning workspace");
   if (e != cudaSuccess) return ctx->cuda_fail(e, "bin_hits");
   ctx->binned = true;

@@ -37,7 +37,7 @@ __global__ void k_bin_keys(const GeomDev* __restrict__ gdev, const float* __rest
                            const float* __restrict__ lcov, const int* __restrict__ layer, int64_t n_hits,
                            const int64_t* __restrict__ ev_off, int n_events, int* __restrict__ keys,
                            int* __restrict__ ranks, int* __restrict__ counts, float* __restrict__ vmax,
-                           int* __restrict__ status) {
+                           const uint8_t* __restrict__ mask, int* __restrict__ status) {
   __shared__ int sv[2][MKF_MAX_LAYERS][2];   // float bits; variances are >= 0, so int order = float order
   __shared__ int e_first;
   const int L = gdev->n_layers;
@@ -51,6 +51,8 @@ __global__ void k_bin_keys(const GeomDev* __restrict__ gdev, const float* __rest
     if (l < 0 || l >= L) {
       keys[h] = -1;
       atomicOr(status, kStatBadInput);
+    } else if (mask && mask[h]) {
+      keys[h] = -1;   // masked: left out of every bin, so no search can return it
     } else {
       const LayerDev ly = gdev->L[l];
       const float x = xyz[h], y = xyz[n_hits + h], z = xyz[2 * n_hits + h];
@@ -219,10 +221,36 @@ __global__ void k_bin_order(const int* __restrict__ bin_off, int64_t n_bins, flo
   }
 }
 
+// mask[h] = 1 for every hit of a track whose flag is MKF_TRK_KEPT
+__global__ void k_used_hits(const int* __restrict__ hits, const int* __restrict__ flags, int64_t n_tracks, int L,
+                            int64_t n_hits, uint8_t* __restrict__ mask, int* __restrict__ status) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_tracks * L) return;
+  const int64_t t = i / L;
+  if (flags[t] != MKF_TRK_KEPT) return;
+  const int h = hits[i];
+  if (h < 0) return;
+  if (h >= n_hits) {
+    atomicOr(status, kStatBadInput);
+    return;
+  }
+  mask[h] = 1;
+}
+
 }  // namespace
 
+cudaError_t launch_used_hits(mkf_ctx* ctx, const int* hits, const int* flags, int64_t n_tracks, int L,
+                             int64_t n_hits, uint8_t* mask, cudaStream_t st) {
+  const int64_t n = n_tracks * L;
+  if (n == 0) return cudaSuccess;
+  const int T = 256;
+  k_used_hits<<<(unsigned)((n + T - 1) / T), T, 0, st>>>(hits, flags, n_tracks, L, n_hits, mask,
+                                                         ctx->status.as<int>());
+  return cudaGetLastError();
+}
+
 cudaError_t launch_bin_hits(mkf_ctx* ctx, const float* xyz, const float* lcov, const int* layer, int64_t n_hits,
-                            const int64_t* ev_hit_off, int n_events, cudaStream_t st) {
+                            const int64_t* ev_hit_off, int n_events, const uint8_t* mask, cudaStream_t st) {
   const GeomDev& g = ctx->geom;
   const int64_t n_bins = (int64_t)n_events * g.bins_per_event;
   const int64_t n_parts = (n_bins + kScanTile - 1) / kScanTile;
@@ -252,7 +280,7 @@ cudaError_t launch_bin_hits(mkf_ctx* ctx, const float* xyz, const float* lcov, c
   if (H > 0) {
     k_bin_keys<<<(unsigned)((H + T - 1) / T), T, 0, st>>>(gd, xyz, lcov, layer, H, ctx->ev_hit_off.as<int64_t>(),
                                                          n_events, ctx->keys.as<int>(), ctx->ranks.as<int>(),
-                                                         ctx->bin_cnt.as<int>(), ctx->vmax.as<float>(), status);
+                                                         ctx->bin_cnt.as<int>(), ctx->vmax.as<float>(), mask, status);
   }
   k_scan_reduce<<<(unsigned)n_parts, kScanThreads, 0, st>>>(ctx->bin_cnt.as<int>(), n_bins, ctx->scan_part.as<int>());
   k_scan_partials<<<1, 1024, 0, st>>>(ctx->scan_part.as<int>(), (int)n_parts);

@@ -112,6 +112,7 @@ struct mkf_ctx {
 
   // build / dedup
   mkf::DevBuf seed_ctr, stats, status, dd_head, dd_next, dd_beat, dd_nbeat, dd_state, track_hits;
+  mkf::DevBuf probe_buf;   // output of the FP32 throughput probe
 
   // optional stage timing (CUDA events on the launch stream)
   int timing = 0;
@@ -142,7 +143,9 @@ namespace mkf {
 // launchers (each returns the first CUDA error, or cudaSuccess)
 cudaError_t launch_bin_order(mkf_ctx* ctx, cudaStream_t st);
 cudaError_t launch_bin_hits(mkf_ctx* ctx, const float* xyz, const float* lcov, const int* layer, int64_t n_hits,
-                            const int64_t* ev_hit_off, int n_events, cudaStream_t st);
+                            const int64_t* ev_hit_off, int n_events, const uint8_t* mask, cudaStream_t st);
+cudaError_t launch_used_hits(mkf_ctx* ctx, const int* hits, const int* flags, int64_t n_tracks, int L,
+                             int64_t n_hits, uint8_t* mask, cudaStream_t st);
 cudaError_t launch_build(mkf_ctx* ctx, const BuildArgs& a, cudaStream_t st);
 cudaError_t launch_dedup(mkf_ctx* ctx, const int* hits, int L, const float* score, const int* nhits,
                          const int64_t* ev_seed_off, int n_events, int64_t n_seeds, int64_t n_hits_total,

@@ -264,3 +264,44 @@ def test_dedup_matches_oracle_on_oracle_tracks():
     exp = oracle.dedup(hits, score.astype(np.float64), nh, 4, 0.5)
     assert np.array_equal(flags.cpu().numpy(), exp)
     ctx.close()
+
+
+def test_two_iterations_with_hit_masking():
+    """Iterative tracking (Sec. 3): the hits of the tracks kept by a first
+    building iteration are masked for a second iteration with other seeds.
+    The second iteration never returns a masked hit and equals the oracle run
+    on the remaining hits only."""
+    import paper_2002_06295_gb300 as mkf
+    ev = synth.make_config_event(1)
+    dev = torch.device("cuda", 0)
+    ctx = make_ctx(ev.geom)
+    xyz, lcov, lay = f32(ev.hit_xyz.T, dev), f32(ev.hit_lcov.T, dev), i32(ev.hit_layer, dev)
+    hoff = i64([0, ev.n_hits], dev)
+    A, B = np.arange(0, ev.n_seeds, 2), np.arange(1, ev.n_seeds, 2)
+    mkf.mkf_bin_hits(ctx, xyz, lcov, lay, hoff)
+    o1 = mkf.mkf_build_tracks(ctx, f32(ev.seed_par[A].T, dev), f32(ev.seed_cov[A].T, dev), i64([0, A.size], dev),
+                              max_cands=4)
+    mask = mkf.mkf_used_hits(ctx, o1["hits"], o1["flags"], ev.n_hits)
+    mkf.mkf_bin_hits_masked(ctx, xyz, lcov, lay, hoff, mask=mask)
+    o2 = mkf.mkf_build_tracks(ctx, f32(ev.seed_par[B].T, dev), f32(ev.seed_cov[B].T, dev), i64([0, B.size], dev),
+                              max_cands=4)
+    mkf.mkf_sync(ctx)
+    m = mask.cpu().numpy().astype(bool)
+    h1, f1 = o1["hits"].cpu().numpy(), o1["flags"].cpu().numpy()
+    used = np.unique(h1[(f1 == mkf.TRK_KEPT)][h1[(f1 == mkf.TRK_KEPT)] >= 0])
+    assert m.sum() == used.size and m[used].all()
+    h2 = o2["hits"].cpu().numpy()
+    assert not m[h2[h2 >= 0]].any()
+    # the oracle on the hits that are left, ids mapped back to the caller's
+    keep = np.nonzero(~m)[0]
+    sub = synth.Event(**{**ev.__dict__})
+    sub.hit_xyz, sub.hit_lcov, sub.hit_layer = ev.hit_xyz[keep], ev.hit_lcov[keep], ev.hit_layer[keep]
+    sub.seed_par, sub.seed_cov = ev.seed_par[B], ev.seed_cov[B]
+    r = oracle_build([sub], max_cands=4, dedup=False)
+    r["hits"] = np.where(r["hits"] >= 0, keep[np.maximum(r["hits"], 0)], -1)
+    g = {k: v.cpu().numpy() for k, v in o2.items()}
+    g["par"] = g["par"].T.astype(np.float64)
+    g["cov"] = g["cov"].T.astype(np.float64)
+    g["nhits"], g["nholes"], g["nsteps"] = g["counts"]
+    _assert_parity(compare(g, r))
+    ctx.close()
