@@ -380,6 +380,18 @@ def profiled_traffic(workload):
     return int(kv["dram-bytes-per-launch"])
 
 
+def rank_reduce(dist, dev, values, op):
+    """Reduce a list of numbers over the ranks ("max", "min" or "sum"); the
+    identity on one rank.  Used for the slowest rank's times, the total work of
+    all ranks and decisions every rank must take alike."""
+    if not dist:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op={"max": dist.ReduceOp.MAX, "min": dist.ReduceOp.MIN, "sum": dist.ReduceOp.SUM}[op])
+    return [float(x) for x in t.tolist()]
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -543,11 +555,7 @@ def main():
             torch.cuda.synchronize()
         except Exception as exc:   # capture refused: eager numbers stand
             graphs, graph_note = {}, "%s: %s" % (type(exc).__name__, str(exc).splitlines()[0][:160])
-        ok = 1 if graphs else 0
-        if dist:   # replay only if every rank captured
-            t = torch.tensor([ok], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MIN)
-            ok = int(t.item())
+        ok = int(rank_reduce(dist, dev, [1 if graphs else 0], "min")[0])   # replay only if every rank captured
         if ok:
             if dist:
                 dist.barrier()
@@ -567,10 +575,9 @@ def main():
         mkf.mkf_set_timing(ctx, True)
         mkf.mkf_sync(ctx)
     clk = clocks.stop()
-    if dist:   # every rank takes the slowest rank's times and the same launch mode
-        t = torch.tensor([eager_ms, graph_ms if graph_ms is not None else float("inf")], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        eager_ms, graph_ms = float(t[0].item()), (float(t[1].item()) if t[1].item() < float("inf") else None)
+    # every rank takes the slowest rank's times and the same launch mode
+    eager_ms, gm = rank_reduce(dist, dev, [eager_ms, graph_ms if graph_ms is not None else float("inf")], "max")
+    graph_ms = gm if gm < float("inf") else None
     use_graph = graph_ms is not None and graph_ms < eager_ms
     total_ms = graph_ms if use_graph else eager_ms
 
@@ -602,6 +609,9 @@ def main():
         b.synchronize()
         e2e_ms.append(a.elapsed_time(b))
     mkf.mkf_sync(ctx)
+    # whole-job figures: the work of all ranks over the slowest rank's time
+    units = rank_reduce(dist, dev, [stats["cand_steps"]], "sum")[0]
+    e2e_total = rank_reduce(dist, dev, [sum(e2e_ms)], "max")[0]
 
     if rank != 0:
         return
@@ -610,9 +620,8 @@ def main():
         from paper_2002_06295_gb300 import tune as _tune
         secondary = {"batched_vs_plain": measure_batched(mkf, _tune, dev),
                      "fit_gradient": measure_fit_gradient(mkf, dev)}
-    units = stats["cand_steps"] * world
     value = units * args.steps / (total_ms * 1e-3)
-    e2e_value = units * args.steps / (sum(e2e_ms) * 1e-3)
+    e2e_value = units * args.steps / (e2e_total * 1e-3)
     b_ms = statistics.mean(build_ms)
     alg_flops = (stats["nav_tests"] * FLOPS_NAV_TEST + stats["cand_steps"] * FLOPS_CAND_STEP
                  + stats["chi2_evals"] * FLOPS_BOX + stats["chi2_full"] * FLOPS_CHI2
@@ -649,7 +658,7 @@ def main():
                      "algorithmic_flops_per_launch": alg_flops},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "ms_per_step": statistics.mean(e2e_ms)},
+                "ms_per_step": e2e_total / args.steps},
         "gpu_launches": launches_per_step * args.steps,
         "launch_ms_per_step": {"eager": eager_ms / args.steps,
                                "cuda_graph": None if graph_ms is None else graph_ms / args.steps,
