@@ -384,12 +384,11 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
     float ns = INFINITY;
     HelixPt<float> hn;        // the helix at a disk crossing found by the navigation
     bool have_hn = false;
-    float sin_t = 1.f, cos_t = 0.f, cot_t = 0.f, omega = 0.f;
+    float sin_t = 1.f, cos_t = 0.f, cot_t = 0.f, omega = 0.f, sph = 0.f, cph = 1.f;
     if (active && step < L) {
       msincos(p[5], &sin_t, &cos_t);
       cot_t = cos_t / sin_t;
       omega = ck * p[3];
-      float sph, cph;
       msincos(p[4], &sph, &cph);
       // surfaces already passed form a prefix of each sorted list
       for (int i = first_above(G.barrel_r, G.n_barrel, rho + kNavEps); i < G.n_barrel; ++i) {
@@ -424,7 +423,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
             exit_known = true;
             if (!(s < s_lim)) break;
           }
-          const auto h = helix_at(p[0], p[1], p[2], p[4], cot_t, omega, s);
+          const auto h = helix_at(p[0], p[1], p[2], p[4], cph, sph, cot_t, omega, s);
           const float r = sqrtf(fmaf(h.x, h.x, h.y * h.y));
           if (r >= ly.lo && r <= ly.hi) {
             nl = l;
@@ -444,7 +443,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
       ++n_steps;
       const LayerDev ly = G.L[nl];
       const int kind = ly.kind;
-      const auto h = have_hn ? hn : helix_at(p[0], p[1], p[2], p[4], cot_t, omega, ns);
+      const auto h = have_hn ? hn : helix_at(p[0], p[1], p[2], p[4], cph, sph, cot_t, omega, ns);
       const auto J = transport_jacobian(kind, p, h, ns, omega, ck, cot_t, sin_t);
       float ms_phi = 0.0f, ms_theta = 0.0f;
       if (ly.x0 > 0.0f) {

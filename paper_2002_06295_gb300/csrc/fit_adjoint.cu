@@ -63,15 +63,15 @@ __device__ __forceinline__ float prop_pass(int e, const float p0[6], const FitHi
   msincos(q[5], &st, &ct);
   const DF cot = ct / st;
   const DF om = DF(ck) * q[3];
+  DF sph, cph;
+  msincos(q[4], &sph, &cph);
   DF sd;
   if (f.kind == 0) {
-    DF sph, cph;
-    msincos(q[4], &sph, &cph);
     sd = cylinder_path(q[0], q[1], cph, sph, om, posd, +1);
   } else {
     sd = plane_path(q[2], cot, posd, +1);
   }
-  const auto hd = helix_at(q[0], q[1], q[2], q[4], cot, om, sd);
+  const auto hd = helix_at(q[0], q[1], q[2], q[4], cph, sph, cot, om, sd);
   const auto Jd = transport_jacobian(f.kind, q, hd, sd, om, DF(ck), cot, st);
   float acc_e = fmaf(ppb[0], hd.x.d, fmaf(ppb[1], hd.y.d, fmaf(ppb[2], hd.z.d, ppb[4] * hd.phi.d)));
   if (e == 3) acc_e += ppb[3];
@@ -126,19 +126,19 @@ __global__ void __launch_bounds__(kAdjThreads)
 
       // ---------------- forward recompute of the step
       float sin_t, cos_t;
-      sincosf(p0[5], &sin_t, &cos_t);
+      msincos(p0[5], &sin_t, &cos_t);
       const float cot_t = cos_t / sin_t;
       const float omega = ck * p0[3];
+      float sph, cph;
+      msincos(p0[4], &sph, &cph);
       float s;
       if (f.kind == 0) {
-        float sph, cph;
-        sincosf(p0[4], &sph, &cph);
         s = cylinder_path(p0[0], p0[1], cph, sph, omega, f.pos, +1);
       } else {
         s = plane_path(p0[2], cot_t, f.pos, +1);
       }
       if (!(fabsf(s) < INFINITY)) continue;
-      const auto hp = helix_at(p0[0], p0[1], p0[2], p0[4], cot_t, omega, s);
+      const auto hp = helix_at(p0[0], p0[1], p0[2], p0[4], cph, sph, cot_t, omega, s);
       const auto J4 = transport_jacobian(f.kind, p0, hp, s, omega, ck, cot_t, sin_t);
       float C2[21];
 #pragma unroll

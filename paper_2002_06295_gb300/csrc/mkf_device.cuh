@@ -66,19 +66,6 @@ template <class T> __device__ __forceinline__ T wrap_phi(T a) {
   return a - T(2.0 * kPiD) * mrint(a * T(1.0 / (2.0 * kPiD)));
 }
 
-// sin(u)/u and its derivative, series near 0 (|u| < 0.1: next terms < 1e-11).
-template <class T> __device__ __forceinline__ void sinc_and_deriv(T u, T su, T cu, T& sc, T& dsc) {
-  if (mabs(vv(u)) < 0.1f) {
-    T u2 = u * u;
-    sc = T(1.0) - u2 * T(1.0 / 6.0) * (T(1.0) - u2 * T(1.0 / 20.0) * (T(1.0) - u2 * T(1.0 / 42.0)));
-    dsc = -u * T(1.0 / 3.0) * (T(1.0) - u2 * T(1.0 / 10.0) * (T(1.0) - u2 * T(1.0 / 28.0)));
-  } else {
-    T iu = T(1.0) / u;
-    sc = su * iu;
-    dsc = (cu - sc) * iu;
-  }
-}
-
 // Convert a root sigma = tan(omega s / 2) / omega of the crossing equation
 // into the transverse path s in the requested direction (dir > 0: s > 0,
 // smallest; dir < 0: s < 0, smallest |s|).  atan(t)/t -> 1 keeps omega -> 0
@@ -151,16 +138,30 @@ template <class T> struct HelixPt {
   T dx_dom, dy_dom; // d x / d omega, d y / d omega at fixed s
 };
 
+// (cphi0, sphi0) = cos/sin of phi0, which every caller needs anyway; the
+// azimuth at the chord, phi0 + u, is then obtained by angle addition.  For
+// |u| < 0.1 sin u, cos u, sinc u = sin(u)/u and its derivative come from their
+// series (first omitted terms below 3e-14 relative), else from sincos.
 template <class T>
-__device__ __forceinline__ HelixPt<T> helix_at(T x0, T y0, T z0, T phi0, T cot_t, T omega, T s) {
+__device__ __forceinline__ HelixPt<T> helix_at(T x0, T y0, T z0, T phi0, T cphi0, T sphi0, T cot_t, T omega, T s) {
   HelixPt<T> h;
   T u = T(0.5) * omega * s;
-  T su, cu;
-  msincos(u, &su, &cu);
-  T sc, dsc;
-  sinc_and_deriv(u, su, cu, sc, dsc);
-  T sp, cp;
-  msincos(phi0 + u, &sp, &cp);
+  T su, cu, sc, dsc;
+  if (mabs(vv(u)) < 0.1f) {
+    const T u2 = u * u;
+    sc = T(1.0) - u2 * T(1.0 / 6.0) * (T(1.0) - u2 * T(1.0 / 20.0) * (T(1.0) - u2 * T(1.0 / 42.0)));
+    dsc = -u * T(1.0 / 3.0) * (T(1.0) - u2 * T(1.0 / 10.0) * (T(1.0) - u2 * T(1.0 / 28.0)));
+    su = u * sc;
+    cu = T(1.0) - T(0.5) * u2 * (T(1.0) - u2 * T(1.0 / 12.0) * (T(1.0) - u2 * T(1.0 / 30.0) *
+                                                                       (T(1.0) - u2 * T(1.0 / 56.0))));
+  } else {
+    msincos(u, &su, &cu);
+    const T iu = T(1.0) / u;
+    sc = su * iu;
+    dsc = (cu - sc) * iu;
+  }
+  const T cp = cphi0 * cu - sphi0 * su;   // cos(phi0 + u)
+  const T sp = sphi0 * cu + cphi0 * su;   // sin(phi0 + u)
   T f = s * sc;
   h.x = mfma(f, cp, x0);
   h.y = mfma(f, sp, y0);

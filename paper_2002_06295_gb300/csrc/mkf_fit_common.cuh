@@ -74,16 +74,16 @@ template <class T> __device__ __forceinline__ bool step_to(const FitHit<T>& f, T
   msincos(p[5], &sin_t, &cos_t);
   const T cot_t = cos_t / sin_t;
   const T omega = ck * p[3];
+  T sph, cph;
+  msincos(p[4], &sph, &cph);
   T s;
   if (f.kind == 0) {
-    T sph, cph;
-    msincos(p[4], &sph, &cph);
     s = cylinder_path(p[0], p[1], cph, sph, omega, f.pos, dir);
   } else {
     s = plane_path(p[2], cot_t, f.pos, dir);
   }
   if (!(mabs(vv(s)) < INFINITY)) return false;
-  const auto h = helix_at(p[0], p[1], p[2], p[4], cot_t, omega, s);
+  const auto h = helix_at(p[0], p[1], p[2], p[4], cph, sph, cot_t, omega, s);
   const auto J = transport_jacobian(f.kind, p, h, s, omega, ck, cot_t, sin_t);
   similarity(J, C);
   p[0] = h.x;
