@@ -183,3 +183,43 @@ def test_autograd_function():
     assert torch.allclose(al.grad, ref["g_align"], rtol=1e-4, atol=1e-6 * float(ref["g_align"].abs().max()))
     assert torch.allclose(xx.grad, ref["g_x0"], rtol=1e-4, atol=1e-6 * float(ref["g_x0"].abs().max()))
     ctx.close()
+
+
+def test_fit_gradient_full_size_sampled_tracks():
+    """C4 at full size (100k tracks x 14 hits, barrel of 14 cylinders) in one
+    launch as the bench times it.  Each hit belongs to one track, so the
+    gradient of sum chi2 with respect to a sampled track's hits is that track's
+    alone: it is compared, with the track's chi2, against the oracle's
+    dual-number gradient of that track."""
+    import oracle
+    import paper_2002_06295_gb300 as mkf
+    g = synth.geometry_barrel14()
+    rng = np.random.default_rng(synth.config_seed(4))
+    ev = synth.simulate_event(g, 100000, rng, pt_range=(1.0, 10.0), eta_max=0.8)
+    keep = (ev.true_hits >= 0).sum(1) == 14
+    hits, sp, sc = ev.true_hits[keep], ev.seed_par[keep], ev.seed_cov[keep]
+    q = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    ev.hit_xyz, ev.hit_lcov = q(ev.hit_xyz), q(ev.hit_lcov)
+    sp, sc = q(sp), q(sc)
+    T, K = hits.shape
+    assert T > 50000
+    dev = torch.device("cuda", 0)
+    ctx = make_ctx(g)
+    xyz_d, lcov_d, lay_d, hits_d = f32(ev.hit_xyz.T, dev), f32(ev.hit_lcov.T, dev), i32(ev.hit_layer, dev), i32(hits, dev)
+    ckpt = torch.empty((K, 27, T), dtype=torch.float32, device=dev)
+    fo = mkf.mkf_fit_tracks(ctx, xyz_d, lcov_d, lay_d, hits_d, f32(sp.T, dev), f32(sc.T, dev), ckpt=ckpt)
+    out = mkf.mkf_fit_tracks_adjoint(ctx, xyz_d, lcov_d, lay_d, hits_d, f32(sp.T, dev), f32(sc.T, dev), ckpt,
+                                     g_chi2=torch.ones(T, dtype=torch.float32, device=dev))
+    mkf.mkf_sync(ctx)
+    gh = out["g_hit"].cpu().numpy().T.astype(np.float64)
+    chi2 = fo["chi2"].cpu().numpy().astype(np.float64)
+    sel = np.random.default_rng(25).choice(T, 60, replace=False)
+    geo = oracle.Geo.of(g)
+    rh, _, _ = oracle.fit_grad(geo, ev.hit_xyz, ev.hit_lcov, ev.hit_layer, hits[sel], sp[sel], sc[sel], np.ones(sel.size))
+    _, _, rchi2, _ = oracle.fit(geo, ev.hit_xyz, ev.hit_lcov, ev.hit_layer, hits[sel], sp[sel], sc[sel])
+    assert np.abs(chi2[sel] - rchi2).max() <= 1e-3 * np.maximum(rchi2, 1.0).max()
+    used = hits[sel].ravel()
+    for c in range(3):
+        emax, enorm = _group_errors(gh[used, c], rh[used, c])
+        assert enorm < GRAD_RTOL and emax < GRAD_RTOL, (c, emax, enorm)
+    ctx.close()

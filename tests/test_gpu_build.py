@@ -305,3 +305,37 @@ def test_two_iterations_with_hit_masking():
     g["nhits"], g["nholes"], g["nsteps"] = g["counts"]
     _assert_parity(compare(g, r))
     ctx.close()
+
+
+def test_batched_full_size_sampled_seeds():
+    """C3 at full size (256 events of 200..8000 tracks, ~561k seeds) in one
+    launch, in the launch configuration the bench's batched measurement picks
+    (256 x 64 bins, 8 warps per block, 4 lanes per seed); 200 seeds sampled
+    over all events are compared with the oracle run on their own event."""
+    import paper_2002_06295_gb300 as mkf
+    b = synth.make_batch(3)
+    ctx = make_ctx(b.geom, 256, 64)
+    mkf.mkf_set_build_config(ctx, 8, 4)
+    g = gpu_build(ctx, b.events, max_cands=4)
+    rng = np.random.default_rng(12)
+    S = int(b.seed_off[-1])
+    pick = np.sort(rng.choice(S, 200, replace=False))
+    ev_of = np.searchsorted(b.seed_off, pick, side="right") - 1
+    rep_total = dict(n=0, robust=0, fragile=0, mismatch_robust=0)
+    for e in np.unique(ev_of):
+        ev = b.events[e]
+        loc = pick[ev_of == e] - b.seed_off[e]
+        r = oracle_build([ev], max_cands=4, seeds=loc, dedup=False)
+        off, hb = int(b.seed_off[e]), int(b.hit_off[e])
+        gi = {k: (v[off:off + ev.n_seeds] if isinstance(v, np.ndarray) and v.shape[:1] == (S,) else v)
+              for k, v in g.items()}
+        gi["hits"] = np.where(gi["hits"] >= 0, gi["hits"] - hb, -1)
+        rep = compare(gi, r, sel=loc)
+        assert rep["mismatch_robust"] == 0, rep
+        if "par_err" in rep:
+            assert rep["par_err"] < PAR_RTOL, rep
+        for k in rep_total:
+            rep_total[k] += rep[k]
+    print("C3 full size, sampled seeds:", rep_total)
+    assert rep_total["fragile"] <= 0.2 * rep_total["n"]
+    ctx.close()
