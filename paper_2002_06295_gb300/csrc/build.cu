@@ -14,16 +14,22 @@
 //  * a seed is owned by a group of GS consecutive lanes of a warp (GS a power
 //    of two >= N = max_cands, chosen per workload); lane k < N of the group
 //    holds candidate slot k (27 floats in registers) for navigation,
-//    propagation, J C J^T and material;
-//  * all GS lanes then scan every candidate's search window together (hits
-//    strided over the lanes), so a wide window -- the seed's first layers --
-//    is shared instead of serialised on one lane; each lane keeps its own best
-//    children (sorted 64-bit keys carrying the parent slot) and the group
-//    merges them with N rounds of shuffle min-reductions;
+//    propagation, J C J^T and material; the propagated state and the search
+//    window go to shared memory, the pre-step state stays in registers;
+//  * the whole warp scans the windows of all its candidates together: the phi
+//    rows of the windows, then the hits of those rows, are dealt to the 32
+//    lanes, and each lane's next hit record is copied to shared memory
+//    (cp.async) while it works on the current one; a box test on the residuals
+//    comes before the chi2;
+//  * an accepted child (64-bit key: score, parent slot, hit index) goes into
+//    its seed's top-N slots in shared memory by an atomicMin cascade, which
+//    leaves the N best in order whatever the interleaving; lane k takes slot k;
 //  * only the selected children are Kalman-updated (the score needs only the
 //    predicted chi2), reading the parent's propagated state from shared memory;
 //  * groups take seeds from a global queue (atomic counter) and refill as soon
 //    as their seed is done, so one launch covers many events of uneven size;
+//    a warp without seeds helps the other warps of its block scan their wide
+//    windows (shared-memory jobs claimed by CAS, every wait bounded);
 //  * the parent pointers and hits of every step stay in shared memory and are
 //    walked back once per seed.
 #include "mkf_device.cuh"
