@@ -18,6 +18,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mkf_oracle.cpp")
+_SRCS = (_SRC, os.path.join(_HERE, "strip_oracle.cpp"))
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -31,10 +32,11 @@ def build(force=False):
     """Compile the oracle (g++, -O2, no target-specific flags)."""
     arch = _LIB + ".arch"
     arch_ok = os.path.exists(arch) and open(arch).read().strip() == platform.machine()
-    if not force and arch_ok and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+    if not force and arch_ok and os.path.exists(_LIB) and \
+            os.path.getmtime(_LIB) >= max(os.path.getmtime(f) for f in _SRCS):
         return _LIB
     tmp = _LIB + ".tmp%d" % os.getpid()
-    subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", tmp, _SRC])
+    subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", tmp] + list(_SRCS))
     os.replace(tmp, _LIB)
     with open(arch, "w") as f:
         f.write(platform.machine())
@@ -70,6 +72,9 @@ def lib():
             L.orc_fit_grad.argtypes = [D, c_int, c_double, D, D, I, c_int, I, c_int, D, D, c_int,
                                        D, D, D, D, D, D, D, D]
             L.orc_fit_grad.restype = c_int
+            P = ctypes.c_void_p
+            L.orc_strip_clusters.argtypes = [c_int, c_int, P, P, P, c_int, c_int, c_int, I, I, I, I, D]
+            L.orc_strip_clusters.restype = c_int
             _lib = L
     return _lib
 
@@ -227,3 +232,23 @@ def fit_grad(geo, hit_xyz, hit_lcov, hit_layer, hits, init_par, init_cov, g_chi2
                        _pd(ic), int(T), _pd(al), _pd(xx), _pd(_d(g_chi2)), _pd(gp), _pd(gc), _pd(gh), _pd(ga),
                        _pd(gx))
     return gh, ga, gx
+
+
+def strip_clusters(adc, noise_q, bad, max_bad_gap=1, q_min=30):
+    """Strip clustering of Sec. 4 on modules [M, N] (adc, noise_q uint16 with
+    noise_q = 8 x noise, bad uint8).  Returns dict of arrays module, first,
+    last, charge (int) and center (charge-weighted strip index), in module
+    order and, within a module, in strip order."""
+    a = np.ascontiguousarray(adc, np.uint16)
+    nq = np.ascontiguousarray(noise_q, np.uint16)
+    b = np.ascontiguousarray(bad, np.uint8)
+    M, N = a.shape
+    cap = max(1, M * (N // 2 + 1))
+    out = {k: np.zeros(cap, np.int32) for k in ("module", "first", "last", "charge")}
+    center = np.zeros(cap)
+    n = lib().orc_strip_clusters(int(M), int(N), a.ctypes.data, nq.ctypes.data, b.ctypes.data, int(max_bad_gap),
+                                 int(q_min), int(cap), _pi(out["module"]), _pi(out["first"]), _pi(out["last"]),
+                                 _pi(out["charge"]), _pd(center))
+    res = {k: v[:n].copy() for k, v in out.items()}
+    res["center"] = center[:n].copy()
+    return res
