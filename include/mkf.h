@@ -114,6 +114,32 @@ mkf_status mkf_bin_hits_masked(mkf_ctx* ctx, const float* xyz, const float* lcov
 mkf_status mkf_used_hits(mkf_ctx* ctx, const int* hits, int L, const int* flags, int64_t n_tracks, int64_t n_hits,
                          uint8_t* mask, void* stream);
 
+/* Strip clustering (Sec. 4, the step before building that turns raw strip
+ * data into hits): in every row r = event * n_modules + module of adc, seed
+ * strips have ADC above 3 times the strip's noise; a cluster adds every strip
+ * above twice the noise that is consecutive or separated only by bad strips,
+ * at most max_bad_gap of them in a row (bad strips carry no charge); it is
+ * kept if sqrt(sum ADC^2) > 5 sqrt(sum noise^2) over its strips and sum ADC
+ * >= q_min.
+ *   adc [n_events * n_modules][n_strips]  uint16 ADC counts (DEVICE)
+ *   noise_q, bad [n_modules][n_strips]    uint16 noise in 1/8 ADC counts (so
+ *                                         every test is exact in integers),
+ *                                         uint8 bad-strip flag (DEVICE)
+ *   out_row, out_first, out_last, out_charge [max_out] int32, out_center
+ *   [max_out] float (charge-weighted strip index) (DEVICE): one entry per
+ *   cluster, in no particular order;
+ *   out_count (DEVICE uint64): number of clusters found, also when it is
+ *   above max_out (then only max_out are written and mkf_sync returns
+ *   MKF_ERR_CAPACITY).
+ * MKF_ERR_ARG for bad sizes or null arrays.  With n_strips a multiple of 16
+ * and 16-byte aligned adc, noise_q and bad, rows are staged by TMA (tensor
+ * maps encoded on each call; MKF_ERR_CUDA if the driver cannot encode them);
+ * any other shape takes a plain kernel with the same results. */
+mkf_status mkf_cluster_strips(mkf_ctx* ctx, const uint16_t* adc, const uint16_t* noise_q, const uint8_t* bad,
+                              int n_events, int n_modules, int n_strips, int max_bad_gap, int q_min, int* out_row,
+                              int* out_first, int* out_last, int* out_charge, float* out_center, int64_t max_out,
+                              unsigned long long* out_count, void* stream);
+
 /* Read back the binning (for inspection and tests): perm [H] original id of
  * each sorted position, bin_off [n_bins_total+1] first sorted position of each
  * (event, layer, bin), n_bins_total = n_events * sum_l(n_phi_l * n_w_l).
@@ -160,6 +186,16 @@ mkf_status mkf_build_tracks(mkf_ctx* ctx, const float* seed_par, const float* se
  * windows, fewer keep more seeds in flight.  Chosen by the autotuner
  * (paper_2002_06295_gb300/tune.py); it changes speed only, never results. */
 mkf_status mkf_set_build_config(mkf_ctx* ctx, int warps_per_block, int lanes_per_seed);
+
+/* Work split of mkf_cluster_strips (TMA path): strips per staged chunk,
+ * events per work item (an item is 32 consecutive modules of that many events,
+ * whose calibration is staged once per chunk) and pipeline stages per warp.
+ * Built splits (chunk, events, stages): (32,1,2) (32,1,3) (32,1,4) (32,2,2)
+ * (64,1,2) (64,1,3) (64,2,2); 0, 0, 0 = default (32,1,2).
+ * Speed only: the clusters found are the same (their order in the output is
+ * not fixed anyway).  MKF_ERR_ARG for any other triple.  The paper has no
+ * counterpart. */
+mkf_status mkf_set_strip_config(mkf_ctx* ctx, int chunk, int events_per_item, int stages);
 
 /* Launch shape of mkf_fit_tracks_adjoint: lanes_per_track 1 (one thread per
  * track), 8 (eight lanes per track share the dual-number passes), or 0 =

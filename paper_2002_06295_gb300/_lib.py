@@ -32,6 +32,8 @@ SIGNATURES = {
     "mkf_set_timing": (i32, [P, i32]),
     "mkf_get_timings": (i32, [P, P, i32, P]),
     "mkf_measure_fp32_peak": (i32, [P, P, P]),
+    "mkf_set_strip_config": (i32, [P, i32, i32, i32]),
+    "mkf_cluster_strips": (i32, [P, P, P, P, i32, i32, i32, i32, i32, P, P, P, P, P, i64, P, P]),
     "mkf_dedup_tracks": (i32, [P, P, i32, P, P, P, i32, i64, i64, i32, f32, P, P]),
     "mkf_dedup_tracks_noalloc": (i32, [P, i32, P, P, P, i32, i64, i64, i32, f32, P, P, P]),
     "mkf_fit_tracks": (i32, [P, P, P, P, i64, P, i32, P, P, i64, P, P, P, P, P, P, P, P]),

@@ -169,6 +169,14 @@ def mkf_set_adjoint_config(ctx, lanes_per_track=0):
     ctx._check(ctx.lib.mkf_set_adjoint_config(ctx.h, int(lanes_per_track)), "mkf_set_adjoint_config")
 
 
+STRIP_CONFIGS = ((32, 1, 2), (32, 1, 3), (32, 1, 4), (32, 2, 2), (64, 1, 2), (64, 1, 3), (64, 2, 2))
+
+
+def mkf_set_strip_config(ctx, chunk=0, events_per_item=0, stages=0):
+    ctx._check(ctx.lib.mkf_set_strip_config(ctx.h, int(chunk), int(events_per_item), int(stages)),
+               "mkf_set_strip_config")
+
+
 def mkf_set_debug(ctx, brute_force_window_check):
     ctx._check(ctx.lib.mkf_set_debug(ctx.h, int(bool(brute_force_window_check))), "mkf_set_debug")
 
@@ -196,6 +204,31 @@ def mkf_get_timings(ctx, stream=None):
     ctx._check(ctx.lib.mkf_get_timings(ctx.h, ctypes.cast(buf, ctypes.c_void_p), 6, _stream(stream)),
                "mkf_get_timings")
     return {k: float(buf[i]) for i, k in enumerate(TIMER_NAMES)}
+
+
+def mkf_cluster_strips(ctx, adc, noise_q, bad, max_bad_gap=1, q_min=30, max_out=None, out=None, stream=None):
+    """Strip clustering of adc [E*M, N] (uint16) with noise_q [M, N] (uint16) and
+    bad [M, N] (uint8).  Returns dict row, first, last, charge, center (device
+    tensors of max_out entries, unordered) and count (device int64 [1])."""
+    R, N = int(adc.shape[0]), int(adc.shape[1])
+    M = int(noise_q.shape[0])
+    if R % M:
+        raise ValueError("adc rows must be a multiple of the module count")
+    dev = adc.device
+    cap = int(max_out) if max_out is not None else max(1, R * N // 8)
+    o = out or dict(row=torch.empty(cap, dtype=torch.int32, device=dev),
+                    first=torch.empty(cap, dtype=torch.int32, device=dev),
+                    last=torch.empty(cap, dtype=torch.int32, device=dev),
+                    charge=torch.empty(cap, dtype=torch.int32, device=dev),
+                    center=torch.empty(cap, dtype=torch.float32, device=dev),
+                    count=torch.zeros(1, dtype=torch.int64, device=dev))
+    cap = int(o["row"].shape[0])
+    ctx._check(ctx.lib.mkf_cluster_strips(ctx.h, _ptr(adc, torch.uint16, "adc"), _ptr(noise_q, torch.uint16, "noise_q"),
+                                          _ptr(bad, torch.uint8, "bad"), R // M, M, N, int(max_bad_gap), int(q_min),
+                                          _ptr(o["row"]), _ptr(o["first"]), _ptr(o["last"]), _ptr(o["charge"]),
+                                          _ptr(o["center"]), cap, _ptr(o["count"], torch.int64, "count"),
+                                          _stream(stream)), "mkf_cluster_strips")
+    return o
 
 
 def mkf_measure_fp32_peak(ctx, stream=None):

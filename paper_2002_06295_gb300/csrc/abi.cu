@@ -58,7 +58,7 @@ void mkf_destroy(mkf_ctx* ctx) {
                     &ctx->bin_cnt,  &ctx->keys,    &ctx->ranks,     &ctx->vmax,     &ctx->ev_hit_off,
                     &ctx->scan_part, &ctx->seed_ctr, &ctx->stats,    &ctx->status,   &ctx->dd_head,
                     &ctx->dd_next,  &ctx->dd_beat, &ctx->dd_nbeat,  &ctx->dd_state, &ctx->track_hits,
-                    &ctx->probe_buf};
+                    &ctx->probe_buf, &ctx->strip_bits};
   for (DevBuf* b : bufs) b->release();
   delete ctx;
 }

@@ -101,6 +101,9 @@ struct mkf_ctx {
   int build_warps = 4;   // warps per block of the building kernel
   int build_group = 0;   // lanes per seed (0: max_cands rounded up to a power of two)
   int adjoint_lanes = 0; // lanes per track of the fit adjoint (0: by track count)
+  int strip_chunk = 0;   // strips per staged chunk of the clustering kernel (0: default)
+  int strip_events = 0;  // events per clustering work item (0: default)
+  int strip_stages = 0;  // pipeline stages per warp of the clustering kernel (0: default)
 
   // binning
   bool binned = false;
@@ -113,6 +116,7 @@ struct mkf_ctx {
   // build / dedup
   mkf::DevBuf seed_ctr, stats, status, dd_head, dd_next, dd_beat, dd_nbeat, dd_state, track_hits;
   mkf::DevBuf probe_buf;   // output of the FP32 throughput probe
+  mkf::DevBuf strip_bits;  // bad-strip flags packed to bits for the clustering kernel
 
   // optional stage timing (CUDA events on the launch stream)
   int timing = 0;
