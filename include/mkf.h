@@ -131,8 +131,8 @@ mkf_status mkf_used_hits(mkf_ctx* ctx, const int* hits, int L, const int* flags,
  *   out_count (DEVICE uint64): number of clusters found, also when it is
  *   above max_out (then only max_out are written and mkf_sync returns
  *   MKF_ERR_CAPACITY).
- * MKF_ERR_ARG for bad sizes or null arrays.  With n_strips a multiple of 16
- * and 16-byte aligned adc, noise_q and bad, rows are staged by TMA (tensor
+ * MKF_ERR_ARG for bad sizes or null arrays.  With n_strips a multiple of 16,
+ * at most 65536, and 16-byte aligned adc, noise_q and bad, rows are staged by TMA (tensor
  * maps encoded on each call; MKF_ERR_CUDA if the driver cannot encode them);
  * any other shape takes a plain kernel with the same results. */
 mkf_status mkf_cluster_strips(mkf_ctx* ctx, const uint16_t* adc, const uint16_t* noise_q, const uint8_t* bad,

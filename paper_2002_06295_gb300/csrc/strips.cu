@@ -77,20 +77,24 @@ __device__ __forceinline__ Cluster run_cluster(const Run& s, int row) {
   return Cluster{row, s.first, s.last, (int)s.q, (float)s.first + (float)s.qi / (float)s.q};
 }
 
-// The same for the TMA kernel, with the sums of squares kept apart so that
-// each strip costs 32 x 32 -> 64-bit multiply-adds only.
+// The same for the TMA kernel (rows of at most 65536 strips, so q < 2^32):
+// sums of squares kept apart so that each strip costs 32 x 32 -> 64-bit
+// multiply-adds only.
 struct RunU {
   int first, last;
   bool open, seeded;
-  unsigned long long q, q2, n2, qi;
+  uint32_t q;
+  unsigned long long q2, n2, qi;
 };
 
 __device__ __forceinline__ bool runu_kept(const RunU& s, int q_min) {
-  return s.open && s.seeded && 64 * s.q2 > 25 * s.n2 && (long long)s.q >= q_min;
+  if (!s.open || !s.seeded || (long long)s.q < q_min) return false;
+  return 64 * s.q2 > 25 * s.n2;
 }
 
 __device__ __forceinline__ Cluster runu_cluster(const RunU& s, int row) {
-  return Cluster{row, s.first, s.last, (int)s.q, (float)s.first + (float)s.qi / (float)s.q};
+  const float qi = fmaf((float)(uint32_t)(s.qi >> 32), 4294967296.0f, (float)(uint32_t)s.qi);
+  return Cluster{row, s.first, s.last, (int)s.q, (float)s.first + qi / (float)s.q};
 }
 
 // ---------------------------------------------------------------------------
@@ -223,6 +227,7 @@ __global__ void __launch_bounds__(kTmaWarps * 32)
                         int* __restrict__ out_last, int* __restrict__ out_charge, float* __restrict__ out_center,
                         int64_t max_out, unsigned long long* __restrict__ count, int* __restrict__ status) {
   using T = TmaShape<CH, E, S>;
+  using Mask = typename std::conditional<CH == 64, unsigned long long, uint32_t>::type;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = smem_raw + ((1024 - (smem_addr(smem_raw) & 1023)) & 1023);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -338,9 +343,12 @@ __global__ void __launch_bounds__(kTmaWarps * 32)
 #pragma unroll
       for (int k = 0; k < E; ++k) run[k].open = false;
     }
+    // masks of the chunk: candidates and breaks (good strips below threshold)
+    Mask cmk[E], brkk[E];
+#pragma unroll
+    for (int k = 0; k < E; ++k) cmk[k] = brkk[k] = 0;
 #pragma unroll
     for (int sb = 0; sb < CH / 32; ++sb) {   // 32-strip blocks of the chunk
-      const int b0 = c * CH + sb * 32;
       // calibration: 0x8000 | floor(nq / 4) per half (4 a > nq <=> a > floor(nq / 4) for integers)
       uint32_t tq[16];
 #pragma unroll
@@ -354,9 +362,7 @@ __global__ void __launch_bounds__(kTmaWarps * 32)
       const uint32_t bm = sbad[sb * 32 + lane];
 #pragma unroll
       for (int k = 0; k < E; ++k) {
-        const int e = h * E + k, r = k * 32 + lane;
-        const bool valid = e < n_events && m < n_modules;
-        const int row = e * n_modules + m;
+        const int r = k * 32 + lane;
         // candidate bits: with a' = min(a, 0x7FFF) (> floor(nq / 4) exactly when a is), the
         // half (0x8000 | floor(nq / 4)) - a' keeps its top bit unless the strip is a candidate
         uint32_t v = 0;
@@ -372,38 +378,49 @@ __global__ void __launch_bounds__(kTmaWarps * 32)
           }
         }
         const uint32_t cm = perfect_shuffle(v) & ~bm;
-        const uint32_t brk = ~(cm | bm);   // good strips below threshold: each one ends a cluster
-        RunU& s = run[k];
-        uint32_t todo = cm;
-        while (todo) {
-          const int p = __ffs(todo) - 1;
-          todo &= todo - 1;
-          const int gi = b0 + p;
-          if (s.open) {   // only bad strips, at most max_bad_gap of them, since the last candidate?
-            const int lo = max(s.last + 1 - b0, 0);
-            const uint32_t between = brk & ((1u << p) - 1u) & (0xFFFFFFFFu << lo);
-            if (between != 0 || gi - s.last - 1 > max_bad_gap) close(s, valid, row);
-          }
-          const int off = swz<T::RB>(r * T::RB + (sb * 32 + p) * 2), noff = swz<T::RB>(lane * T::RB + (sb * 32 + p) * 2);
-          const uint32_t a = *reinterpret_cast<const uint16_t*>(sa + off);
-          const uint32_t nq = *reinterpret_cast<const uint16_t*>(sn + noff);
-          const bool fresh = !s.open;
-          s.first = fresh ? gi : s.first;
-          s.q = (fresh ? 0ull : s.q) + a;
-          s.q2 = (unsigned long long)a * a + (fresh ? 0ull : s.q2);
-          s.n2 = (unsigned long long)nq * nq + (fresh ? 0ull : s.n2);
-          s.qi = (unsigned long long)(uint32_t)(gi - s.first) * a + (fresh ? 0ull : s.qi);
-          s.seeded = (s.seeded && !fresh) || 8 * a > 3 * nq;
-          s.open = true;
-          s.last = gi;
-        }
-        if (s.open) {   // a break after the last candidate, or too many bad strips since it
-          const int lo = s.last + 1 - b0;
-          const uint32_t after = lo <= 0 ? 0xFFFFFFFFu : lo >= 32 ? 0u : 0xFFFFFFFFu << lo;
-          if ((brk & after) != 0 || b0 + 31 - s.last > max_bad_gap) close(s, valid, row);
-        }
-        if (c == nc - 1 && sb == CH / 32 - 1 && s.open) close(s, valid, row);   // end of the row
+        cmk[k] |= (Mask)cm << (32 * sb);
+        brkk[k] |= (Mask)(~(cm | bm)) << (32 * sb);
       }
+    }
+    const int c0 = c * CH;
+    // shared-memory offset of strip p of row r: the swizzle XOR depends on the row only
+    const int nrow = lane * T::RB, nx = swz<T::RB>(nrow) - nrow;
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+      const int e = h * E + k, r = k * 32 + lane;
+      const bool valid = e < n_events && m < n_modules;
+      const int row = e * n_modules + m;
+      const int arow = r * T::RB, ax = swz<T::RB>(arow) - arow;
+      const Mask brk = brkk[k];
+      RunU& s = run[k];
+      Mask todo = cmk[k];
+      while (todo) {
+        const int p = (CH == 64) ? __ffsll((long long)todo) - 1 : __ffs((int)todo) - 1;
+        todo &= todo - 1;
+        const int gi = c0 + p;
+        if (s.open) {   // only bad strips, at most max_bad_gap of them, since the last candidate?
+          const int lo = max(s.last + 1 - c0, 0);
+          const Mask between = brk & (((Mask)1 << p) - 1) & (~(Mask)0 << lo);
+          if (between != 0 || gi - s.last - 1 > max_bad_gap) close(s, valid, row);
+        }
+        const uint32_t a = *reinterpret_cast<const uint16_t*>(sa + arow + ((2 * p) ^ ax));
+        const uint32_t nq = *reinterpret_cast<const uint16_t*>(sn + nrow + ((2 * p) ^ nx));
+        const bool fresh = !s.open;
+        s.first = fresh ? gi : s.first;
+        s.q = (fresh ? 0u : s.q) + a;
+        s.q2 = (unsigned long long)a * a + (fresh ? 0ull : s.q2);
+        s.n2 = (unsigned long long)nq * nq + (fresh ? 0ull : s.n2);
+        s.qi = (unsigned long long)(uint32_t)(gi - s.first) * a + (fresh ? 0ull : s.qi);
+        s.seeded = (s.seeded && !fresh) || 8 * a > 3 * nq;
+        s.open = true;
+        s.last = gi;
+      }
+      if (s.open) {   // a break after the last candidate, or too many bad strips since it
+        const int lo = s.last + 1 - c0;
+        const Mask after = lo <= 0 ? ~(Mask)0 : lo >= CH ? (Mask)0 : ~(Mask)0 << lo;
+        if ((brk & after) != 0 || c0 + CH - 1 - s.last > max_bad_gap) close(s, valid, row);
+      }
+      if (c == nc - 1 && s.open) close(s, valid, row);   // end of the row
     }
     __syncwarp();
     advance(cons);
@@ -613,8 +630,9 @@ extern "C" mkf_status mkf_cluster_strips(mkf_ctx* ctx, const uint16_t* adc, cons
     return ctx->cuda_fail(e, "count");
   const int64_t rows = (int64_t)n_events * n_modules;
   if (rows == 0) return MKF_OK;
-  // TMA needs 16-byte aligned bases and row strides (bad flags: 1 byte a strip)
-  const bool tma = n_strips % 16 == 0 && (uintptr_t)adc % 16 == 0 && (uintptr_t)noise_q % 16 == 0 &&
+  // TMA needs 16-byte aligned bases and row strides (bad flags: 1 byte a strip);
+  // the TMA kernel keeps a cluster's charge in 32 bits (rows of <= 65536 strips)
+  const bool tma = n_strips % 16 == 0 && n_strips <= 65536 && (uintptr_t)adc % 16 == 0 && (uintptr_t)noise_q % 16 == 0 &&
                    (uintptr_t)bad % 16 == 0;
   if (tma) {
     bool encoded = false;
