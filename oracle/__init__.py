@@ -1,7 +1,8 @@
 """FP64 CPU oracle -- TEST INFRASTRUCTURE ONLY.
 
-Plain, slow reference of the combinatorial Kalman-filter building and of the
-fixed-assignment Kalman fit (and its reference gradient).  Only ``tests/``,
+Plain, slow reference of the combinatorial Kalman-filter building, of the
+fixed-assignment Kalman fit (and its reference gradient), of strip clustering
+and of hit-based seeding.  Only ``tests/``,
 ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg may import it;
 the CUDA library never does, and the two share no code.
 
@@ -18,7 +19,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mkf_oracle.cpp")
-_SRCS = (_SRC, os.path.join(_HERE, "strip_oracle.cpp"))
+_SRCS = (_SRC, os.path.join(_HERE, "strip_oracle.cpp"), os.path.join(_HERE, "seed_oracle.cpp"))
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -75,6 +76,9 @@ def lib():
             P = ctypes.c_void_p
             L.orc_strip_clusters.argtypes = [c_int, c_int, P, P, P, c_int, c_int, c_int, I, I, I, I, D]
             L.orc_strip_clusters.restype = c_int
+            L.orc_seed_quads.argtypes = [P, P, ctypes.c_longlong, P, c_int, P, P, c_double, c_double, c_double,
+                                         c_double, c_double, c_double, ctypes.c_longlong, P, P, P, P]
+            L.orc_seed_quads.restype = ctypes.c_longlong
             _lib = L
     return _lib
 
@@ -252,3 +256,45 @@ def strip_clusters(adc, noise_q, bad, max_bad_gap=1, q_min=30):
     res = {k: v[:n].copy() for k, v in out.items()}
     res["center"] = center[:n].copy()
     return res
+
+
+SEED_LAYERS_NEEDED = 4
+
+
+def seeding_layers(geo):
+    """The four innermost barrel layers (ids, radii), innermost first."""
+    kind = np.asarray(geo.kind)
+    pos = np.asarray(geo.pos, np.float64)
+    ids = [int(i) for i in np.argsort(np.where(kind == 0, pos, np.inf), kind="stable") if kind[i] == 0]
+    if len(ids) < SEED_LAYERS_NEEDED:
+        raise ValueError("seeding needs four barrel layers")
+    ids = ids[:SEED_LAYERS_NEEDED]
+    return np.array(ids, np.int32), pos[ids].astype(np.float64)
+
+
+def seed_quads(geo, hit_xyz, hit_layer, ev_hit_off=None, *, pt_min=0.5, z_max=5.0, rphi_tol=0.05, z_tol=0.1,
+               eps=0.0):
+    """Hit-based seeding (Sec. 3, four innermost barrel layers, prompt tracks):
+    every quadruplet whose smallest cut margin is >= -eps.  hit_xyz [H, 3],
+    hit_layer [H]; ev_hit_off [E+1] CSR (default one event).  Returns dict
+    hits [n, 4] (global hit ids), margin [n], par [n, 6] at the beam line,
+    event [n]."""
+    xyz = np.ascontiguousarray(hit_xyz, np.float64)
+    lay = np.ascontiguousarray(hit_layer, np.int32)
+    H = lay.shape[0]
+    off = np.ascontiguousarray([0, H] if ev_hit_off is None else ev_hit_off, np.int64)
+    ids, radii = seeding_layers(geo)
+    cap = 1 << 16
+    while True:
+        hits = np.zeros((cap, 4), np.int32)
+        marg = np.zeros(cap)
+        par = np.zeros((cap, 6))
+        ev = np.zeros(cap, np.int32)
+        n = lib().orc_seed_quads(xyz.ctypes.data, lay.ctypes.data, H, off.ctypes.data, off.size - 1,
+                                 ids.ctypes.data, radii.ctypes.data, float(geo.bz), float(pt_min), float(z_max),
+                                 float(rphi_tol), float(z_tol), float(eps), cap, hits.ctypes.data,
+                                 marg.ctypes.data, par.ctypes.data, ev.ctypes.data)
+        if n <= cap:
+            return {"hits": hits[:n].copy(), "margin": marg[:n].copy(), "par": par[:n].copy(),
+                    "event": ev[:n].copy()}
+        cap = int(n)
