@@ -15,9 +15,17 @@
 //    rphi_tol and z_tol;
 //  * the circle through the origin, a and c and the line through a and c
 //    predict layer 3 the same way for a hit d;
+//  * every hit after a must lie on the predicted side: b within 90 degrees of
+//    a in azimuth, c and d within 90 degrees of their predictions (the sine
+//    residual alone cannot tell a hit from its mirror image through the beam
+//    line, and a pair on opposite sides of it defines a circle that does not
+//    pass outward through both);
 //  * the seed state is at the beam line (0, 0, z0): curvature and direction
 //    from the circle through the origin, b and d, cot theta and z0 from the
-//    line through a and d; kappa = -omega / (alpha Bz).
+//    line through a and d; kappa = -omega / (alpha Bz);
+//  * a circle that does not reach R3 (|omega R3 / 2| >= 1) predicts nothing
+//    (with |omega| <= omega_max and omega_max R3 / 2 < 1 this only happens
+//    to circles through a far-off layer-2 or layer-3 hit).
 // Every cut is reported as a margin 1 - |value| / limit (>= 0: passes), so a
 // caller can tell quadruplets near a cut from the others.  All pairs are tried
 // (no binning).  Shares no code with the CUDA library.
@@ -87,6 +95,7 @@ extern "C" int64_t orc_seed_quads(const double* xyz, const int* layer, int64_t n
         }
     for (const Hit& a : on[0])
       for (const Hit& b : on[1]) {
+        if (a.c * b.c + a.s * b.s <= 0.0) continue;   // opposite sides of the beam line
         const double omega = circle_origin(R0, a, R1, b);
         const double m1 = margin(omega, omega_max);
         if (m1 < -eps) continue;
@@ -95,19 +104,23 @@ extern "C" int64_t orc_seed_quads(const double* xyz, const int* layer, int64_t n
         const double m2 = margin(z0, z_max);
         if (m2 < -eps) continue;
         for (const Hit& c : on[2]) {
+          if (c.c * p2.c + c.s * p2.s <= 0.0) continue;
           const double m3 = margin(R2 * (c.s * p2.c - c.c * p2.s), rphi_tol);
           const double m4 = margin(c.z - p2.z, z_tol);
           if (m3 < -eps || m4 < -eps) continue;
           const double omega2 = circle_origin(R0, a, R2, c);
+          if (std::fabs(0.5 * omega2 * R3) >= 1.0) continue;   // that circle never reaches layer 3
           const Pred p3 = predict(omega2, R0, a, R2, c, R3, nullptr);
           for (const Hit& d : on[3]) {
+            if (d.c * p3.c + d.s * p3.s <= 0.0) continue;
             const double m5 = margin(R3 * (d.s * p3.c - d.c * p3.s), rphi_tol);
             const double m6 = margin(d.z - p3.z, z_tol);
             const double m = std::fmin(std::fmin(std::fmin(m1, m2), std::fmin(m3, m4)), std::fmin(m5, m6));
             if (m < -eps) continue;
+            const double w3 = circle_origin(R1, b, R3, d);
+            if (std::fabs(0.5 * w3 * R3) >= 1.0) continue;
             if (n_out < max_out) {
               // seed state: circle through the origin, b and d; line through a and d
-              const double w3 = circle_origin(R1, b, R3, d);
               const double pb = std::atan2(b.s, b.c);
               const double phi = std::remainder(pb - std::asin(0.5 * w3 * R1), 2.0 * M_PI);
               const double sa = arc_s(w3, R0), sd = arc_s(w3, R3);

@@ -99,6 +99,24 @@ def test_last_layer_residual_margins_closed_form():
         assert abs(r["margin"][0] - (1.0 - abs(dz) / CUTS["z_tol"])) < 1e-9
 
 
+def test_mirror_images_through_the_beam_line_are_not_seeds():
+    """A layer-1 hit on the far side of the beam line defines a nearly straight
+    circle through the origin, and a layer-3 hit turned by pi has the same sine
+    residual: neither may make a seed."""
+    geo = geometry_cmslike()
+    base = (0.0, 1.0 / 20.0, 0.2, 1.3)
+    for k in (1, 3):
+        xyz, lay = _event(geo, [base])
+        xyz[k, 0:2] *= -1.0
+        assert oracle.seed_quads(geo, xyz, lay, eps=0.5, **CUTS)["hits"].shape[0] == 0, k
+    # with both the genuine and the mirrored layer-3 hit only the genuine one is used
+    xyz, lay = _event(geo, [base])
+    xyz = np.concatenate([xyz, xyz[3:4] * np.array([-1.0, -1.0, 1.0])])
+    lay = np.concatenate([lay, lay[3:4]])
+    r = oracle.seed_quads(geo, xyz, lay, **CUTS)
+    assert [list(h) for h in r["hits"]] == [[0, 1, 2, 3]]
+
+
 def _noisy_event():
     ev = sev.make_config_event(2, n_tracks=400)
     return ev.geom, ev.hit_xyz, ev.hit_layer
