@@ -392,6 +392,71 @@ def measure_strips(mkf, dev, reps=5):
                              "sample": "one event (11.5 M strips)"}}
 
 
+# Hit-based seeding: FP32 operations per counted step, read from the kernels in
+# csrc/seeds.cu (FMA = 2, add/mul/div/sqrt/transcendental call = 1).
+FLOPS_SEED_L1 = 40      # a layer-1 hit tested against a layer-0 hit: circle, curvature and z0 cuts
+FLOPS_SEED_PAIR = 59    # a passing pair: cuts again plus the layer-2 prediction
+FLOPS_SEED_L2 = 10      # a layer-2 hit tested against a prediction (side, r-phi and z residuals)
+FLOPS_SEED_TRIP = 58    # a triplet: circle through the origin, layer-0 and layer-2 hits, layer-3 prediction
+FLOPS_SEED_L3 = 10      # a layer-3 hit tested against a prediction
+FLOPS_SEED_SEED = 45    # a seed: final circle and state
+
+
+def measure_seeding(mkf, dev, reps=5):
+    """Hit-based seeding (four innermost barrel layers) on the C3 batch (256
+    events, 5.5 M hits): device time of mkf_seed_tracks (seeding grid, pairs ->
+    triplets, triplets -> seeds), its work counters, the FP32 roofline of that
+    work, and the oracle on one event on one core."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import synth.events as sev
+    cuts = dict(pt_min=0.5, z_max=5.0, rphi_tol=0.15, z_tol=0.3)
+    b = sev.make_batch(3)
+    xyz, lay, lcov = b.cat("hit_xyz"), b.cat("hit_layer"), b.cat("hit_lcov")
+    ctx = mkf.Context(dev.index)
+    mkf.mkf_load_geometry(ctx, b.geom.table(), b.geom.bz, 64, 16)
+    t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(dev, dt)
+    mkf.mkf_bin_hits(ctx, t(xyz.T, torch.float32), t(lcov.T, torch.float32), t(lay, torch.int32),
+                     t(b.hit_off, torch.int64))
+    out = mkf.mkf_seed_tracks(ctx, max_seeds=4 << 20, **cuts)
+    stream = torch.cuda.current_stream()
+    ts = []
+    for r in range(reps + 1):
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        o = mkf.mkf_seed_tracks(ctx, out=out, **cuts)
+        e.record(stream)
+        e.synchronize()
+        if r:
+            ts.append(a.elapsed_time(e))
+    mkf.mkf_sync(ctx)
+    w = mkf.mkf_get_seed_stats(ctx)
+    fma_peak = mkf.mkf_measure_fp32_peak(ctx)
+    ctx.close()
+    ms = min(ts)
+    flops = (w["l1_examined"] * FLOPS_SEED_L1 + w["pairs"] * FLOPS_SEED_PAIR + w["l2_examined"] * FLOPS_SEED_L2
+             + w["triplets"] * FLOPS_SEED_TRIP + w["l3_examined"] * FLOPS_SEED_L3 + w["seeds"] * FLOPS_SEED_SEED)
+    ach = flops / (ms * 1e-3) / 1e12
+    ev0 = b.events[0]
+    t0 = time.perf_counter()
+    ref = oracle.seed_quads(ev0.geom, ev0.hit_xyz, ev0.hit_layer, **cuts)
+    cpu_s = time.perf_counter() - t0
+    return {"workload": "C3: 256 events of the 10-cylinder barrel, %d hits, %d true tracks; cuts %s"
+                        % (int(b.hit_off[-1]), int(b.seed_off[-1]), cuts),
+            "ms": ms, "events_per_s": b.n_events / (ms * 1e-3), "seeds": int(o["n"]),
+            "seeds_per_s": o["n"] / (ms * 1e-3), "work": w,
+            "roofline": {"bound": "alu", "achieved": ach, "peak": fma_peak, "unit": "TFLOP/s",
+                         "frac": ach / fma_peak if fma_peak else None,
+                         "peak_basis": "FP32 FMA probe on this device (mkf_measure_fp32_peak)"},
+            "cpu_baseline": {"value": ev0.n_hits / cpu_s, "unit": "hits/s", "cores": 1, "kind": "oracle",
+                             "sample": "event 0 (%d hits, brute force over all layer-0 x layer-1 pairs)"
+                                       % ev0.n_hits,
+                             "gpu_hits_per_s": int(b.hit_off[-1]) / (ms * 1e-3),
+                             "oracle_seeds": int(ref["hits"].shape[0])}}
+
+
 KERNEL_SOURCES = ("paper_2002_06295_gb300/csrc/build.cu", "paper_2002_06295_gb300/csrc/mkf_device.cuh",
                   "paper_2002_06295_gb300/csrc/mkf_internal.h")
 
@@ -667,7 +732,8 @@ def main():
         from paper_2002_06295_gb300 import tune as _tune
         secondary = {"batched_vs_plain": measure_batched(mkf, _tune, dev),
                      "fit_gradient": measure_fit_gradient(mkf, dev),
-                     "strip_clustering": measure_strips(mkf, dev)}
+                     "strip_clustering": measure_strips(mkf, dev),
+                     "seeding": measure_seeding(mkf, dev)}
     value = units * args.steps / (total_ms * 1e-3)
     e2e_value = units * args.steps / (e2e_total * 1e-3)
     b_ms = statistics.mean(build_ms)

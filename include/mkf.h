@@ -140,6 +140,49 @@ mkf_status mkf_cluster_strips(mkf_ctx* ctx, const uint16_t* adc, const uint16_t*
                               int* out_first, int* out_last, int* out_charge, float* out_center, int64_t max_out,
                               unsigned long long* out_count, void* stream);
 
+/* Hit-based seeding of prompt tracks from the four innermost barrel layers
+ * (Sec. 3: the initial iteration seeds from the four innermost pixel layers
+ * and targets prompt tracks; the rules are this library's reading).  Uses the
+ * hits of the last mkf_bin_hits / mkf_bin_hits_masked, all events:
+ *  - a pair (layer 0, layer 1) defines the circle through the beam line
+ *    (origin) and both hits and the line z = z0 + s cot(theta) in the
+ *    transverse path s; it passes if its curvature |omega| <= alpha Bz / pt_min
+ *    (pt_min in GeV) and |z0| <= z_max (cm);
+ *  - that helix predicts layer 2: a hit passes if its transverse residual
+ *    R2 sin(phi_hit - phi_pred) and its z residual are within rphi_tol and
+ *    z_tol (cm); the helix through the origin and the layer-0 and layer-2
+ *    hits predicts layer 3 the same way;
+ *  - the layer-1 hit lies within 90 degrees of the layer-0 hit in azimuth,
+ *    the layer-2 and layer-3 hits within 90 degrees of their predictions;
+ *  - every passing quadruplet is a seed; its state is on the beam line,
+ *    (0, 0, z0, kappa, phi, theta), from the circle through the origin and the
+ *    layer-1 and layer-3 hits and the line through the layer-0 and layer-3
+ *    hits, with a fixed diagonal covariance (sigma x, y 0.01 cm, z 0.05 cm,
+ *    kappa 5 % + 0.01 /GeV, phi and theta 5 mrad).
+ * Decisions are taken in FP32.  The call synchronises `stream` once (it reads
+ * back the number of hit pairs to size its working memory), so it cannot be
+ * captured in a CUDA graph.  Outputs (DEVICE, caller-owned):
+ *   ev_seed_off [n_events + 1] int64: seeds of event e are [off[e], off[e+1]);
+ *     n = ev_seed_off[n_events] is the number found;
+ *   seed_par [6][n], seed_cov [21][n] float: laid out with column stride n
+ *     (so the first 6 n and 21 n floats are ready for mkf_build_tracks);
+ *     buffers hold max_seeds columns;
+ *   seed_hits [n][4] int: caller hit ids on layers 0..3.
+ * If n > max_seeds nothing but ev_seed_off is written and mkf_sync returns
+ * MKF_ERR_CAPACITY.  The seeds are in a fixed order (event, then layer-0 hit
+ * by bin and id, then the search order).  MKF_ERR_STATE without geometry or
+ * binned hits; MKF_ERR_ARG for fewer than four barrel layers, non-positive
+ * cuts, pt_min so low that a circle of the largest allowed curvature does not
+ * reach 1.1 times the layer-3 radius, or rphi_tol >= R2 / 2. */
+mkf_status mkf_seed_tracks(mkf_ctx* ctx, float pt_min, float z_max, float rphi_tol, float z_tol, int64_t max_seeds,
+                           float* seed_par, float* seed_cov, int* seed_hits, int64_t* ev_seed_off, void* stream);
+
+/* Work counters of the last mkf_seed_tracks (synchronises `stream`): [0]
+ * layer-1 hits examined in the pair windows, [1] pairs that passed, [2]
+ * layer-2 hits examined, [3] triplets, [4] layer-3 hits examined, [5] seeds.
+ * HOST output of n <= 6 values (zeros before the first call). */
+mkf_status mkf_get_seed_stats(mkf_ctx* ctx, int64_t* out, int n, void* stream);
+
 /* Read back the binning (for inspection and tests): perm [H] original id of
  * each sorted position, bin_off [n_bins_total+1] first sorted position of each
  * (event, layer, bin), n_bins_total = n_events * sum_l(n_phi_l * n_w_l).

@@ -231,6 +231,43 @@ def mkf_cluster_strips(ctx, adc, noise_q, bad, max_bad_gap=1, q_min=30, max_out=
     return o
 
 
+def mkf_seed_tracks(ctx, pt_min=0.5, z_max=5.0, rphi_tol=0.05, z_tol=0.1, max_seeds=None, out=None, stream=None):
+    """Hit-based seeding (four innermost barrel layers) from the binned hits.
+    Returns dict par [6, n], cov [21, n] (views ready for mkf_build_tracks),
+    hits [n, 4], ev_seed_off [E+1] (device int64) and n (read back, one
+    synchronising copy)."""
+    dev = torch.device("cuda", ctx.device)
+    cap = int(max_seeds) if max_seeds is not None else max(1024, int(ctx.n_hits))
+    E = int(ctx.n_events)
+    o = out or dict(par=torch.empty(6 * cap, dtype=torch.float32, device=dev),
+                    cov=torch.empty(21 * cap, dtype=torch.float32, device=dev),
+                    hits=torch.empty(4 * cap, dtype=torch.int32, device=dev),
+                    ev_seed_off=torch.empty(E + 1, dtype=torch.int64, device=dev))
+    cap = int(o["hits"].numel()) // 4
+    ctx._check(ctx.lib.mkf_seed_tracks(ctx.h, float(pt_min), float(z_max), float(rphi_tol), float(z_tol), cap,
+                                       _ptr(o["par"]), _ptr(o["cov"]), _ptr(o["hits"]),
+                                       _ptr(o["ev_seed_off"], torch.int64, "ev_seed_off"), _stream(stream)),
+               "mkf_seed_tracks")
+    n = int(o["ev_seed_off"][E].item())
+    res = dict(o)
+    res["n"] = n
+    if n <= cap:
+        res["par"] = o["par"][:6 * n].view(6, n)
+        res["cov"] = o["cov"][:21 * n].view(21, n)
+        res["hits"] = o["hits"][:4 * n].view(n, 4)
+    return res
+
+
+SEED_STAT_NAMES = ("l1_examined", "pairs", "l2_examined", "triplets", "l3_examined", "seeds")
+
+
+def mkf_get_seed_stats(ctx, stream=None):
+    buf = (ctypes.c_int64 * len(SEED_STAT_NAMES))()
+    ctx._check(ctx.lib.mkf_get_seed_stats(ctx.h, ctypes.cast(buf, ctypes.c_void_p), len(SEED_STAT_NAMES),
+                                          _stream(stream)), "mkf_get_seed_stats")
+    return {k: int(buf[i]) for i, k in enumerate(SEED_STAT_NAMES)}
+
+
 def mkf_measure_fp32_peak(ctx, stream=None):
     v = (ctypes.c_float * 1)()
     ctx._check(ctx.lib.mkf_measure_fp32_peak(ctx.h, ctypes.cast(v, ctypes.c_void_p), _stream(stream)),

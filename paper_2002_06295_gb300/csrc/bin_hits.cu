@@ -249,6 +249,17 @@ cudaError_t launch_used_hits(mkf_ctx* ctx, const int* hits, const int* flags, in
   return cudaGetLastError();
 }
 
+cudaError_t launch_excl_scan(const int* in, int64_t n, int* out, DevBuf& part, cudaStream_t st) {
+  cudaError_t e;
+  if (n <= 0) return cudaMemsetAsync(out, 0, sizeof(int), st);
+  const int64_t n_parts = (n + kScanTile - 1) / kScanTile;
+  if ((e = part.ensure((size_t)n_parts * 4)) != cudaSuccess) return e;
+  k_scan_reduce<<<(unsigned)n_parts, kScanThreads, 0, st>>>(in, n, part.as<int>());
+  k_scan_partials<<<1, 1024, 0, st>>>(part.as<int>(), (int)n_parts);
+  k_scan_apply<<<(unsigned)n_parts, kScanThreads, 0, st>>>(in, n, part.as<int>(), out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_bin_hits(mkf_ctx* ctx, const float* xyz, const float* lcov, const int* layer, int64_t n_hits,
                             const int64_t* ev_hit_off, int n_events, const uint8_t* mask, cudaStream_t st) {
   const GeomDev& g = ctx->geom;

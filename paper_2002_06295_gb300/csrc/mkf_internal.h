@@ -117,6 +117,9 @@ struct mkf_ctx {
   mkf::DevBuf seed_ctr, stats, status, dd_head, dd_next, dd_beat, dd_nbeat, dd_state, track_hits;
   mkf::DevBuf probe_buf;   // output of the FP32 throughput probe
   mkf::DevBuf strip_bits;  // bad-strip flags packed to bits for the clustering kernel
+  mkf::DevBuf seed_cnt, seed_off, seed_part, seed_pairs, seed_qcnt, seed_qoff;   // hit-based seeding
+  mkf::DevBuf grid_key, grid_rank, grid_cnt, grid_off, grid_rec;                // its search grid
+  mkf::DevBuf seed_stats;                                                       // its work counters
 
   // optional stage timing (CUDA events on the launch stream)
   int timing = 0;
@@ -146,6 +149,8 @@ struct mkf_ctx {
 namespace mkf {
 // launchers (each returns the first CUDA error, or cudaSuccess)
 cudaError_t launch_bin_order(mkf_ctx* ctx, cudaStream_t st);
+// out[i] = in[0] + ... + in[i-1] for i <= n (out has n + 1 entries); part is scratch
+cudaError_t launch_excl_scan(const int* in, int64_t n, int* out, DevBuf& part, cudaStream_t st);
 cudaError_t launch_bin_hits(mkf_ctx* ctx, const float* xyz, const float* lcov, const int* layer, int64_t n_hits,
                             const int64_t* ev_hit_off, int n_events, const uint8_t* mask, cudaStream_t st);
 cudaError_t launch_used_hits(mkf_ctx* ctx, const int* hits, const int* flags, int64_t n_tracks, int L,
