@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c5"],
                     help="timed workload (c2: the CMS-like event the metric is quoted on)")
     ap.add_argument("--no-graph", action="store_true", help="time eager launches only (no CUDA-graph replay)")
+    ap.add_argument("--only", choices=["strips", "seeding"],
+                    help="run one secondary measurement alone and print it (for profiling its kernel)")
     return ap.parse_args()
 
 
@@ -387,6 +389,7 @@ def measure_strips(mkf, dev, reps=5):
             "clusters": n, "clusters_per_event_oracle": int(ref["module"].size),
             "roofline": {"bound": "hbm", "achieved": byts / (ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                          "frac": byts / (ms * 1e-3) / 1e9 / hbm, "algorithmic_bytes": byts,
+                         "traffic": profiled_traffic("k_strip_cluster", STRIP_SOURCES),
                          "peak_basis": "MEASURED_PEAKS.json hbm_gbs (measured copy)"},
             "cpu_baseline": {"value": M * N / cpu_s, "unit": "strips/s", "cores": 1, "kind": "oracle",
                              "sample": "one event (11.5 M strips)"}}
@@ -449,6 +452,7 @@ def measure_seeding(mkf, dev, reps=5):
             "seeds_per_s": o["n"] / (ms * 1e-3), "work": w,
             "roofline": {"bound": "alu", "achieved": ach, "peak": fma_peak, "unit": "TFLOP/s",
                          "frac": ach / fma_peak if fma_peak else None,
+                         "traffic": profiled_traffic("k_seed_triplets", SEED_SOURCES),
                          "peak_basis": "FP32 FMA probe on this device (mkf_measure_fp32_peak)"},
             "cpu_baseline": {"value": ev0.n_hits / cpu_s, "unit": "hits/s", "cores": 1, "kind": "oracle",
                              "sample": "event 0 (%d hits, brute force over all layer-0 x layer-1 pairs)"
@@ -459,24 +463,27 @@ def measure_seeding(mkf, dev, reps=5):
 
 KERNEL_SOURCES = ("paper_2002_06295_gb300/csrc/build.cu", "paper_2002_06295_gb300/csrc/mkf_device.cuh",
                   "paper_2002_06295_gb300/csrc/mkf_internal.h")
+STRIP_SOURCES = ("paper_2002_06295_gb300/csrc/strips.cu", "paper_2002_06295_gb300/csrc/mkf_internal.h")
+SEED_SOURCES = ("paper_2002_06295_gb300/csrc/seeds.cu", "paper_2002_06295_gb300/csrc/mkf_device.cuh",
+                "paper_2002_06295_gb300/csrc/mkf_internal.h")
 
 
-def kernel_digest():
-    """sha1 over the building kernel's sources: a profile's counters apply only
-    to the kernel they were taken on."""
+def kernel_digest(sources=KERNEL_SOURCES):
+    """sha1 over a kernel's sources: a profile's counters apply only to the
+    kernel they were taken on."""
     import hashlib
     h = hashlib.sha1()
-    for f in KERNEL_SOURCES:
+    for f in sources:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
 
 
-def profiled_traffic(workload):
-    """DRAM bytes (read + write) per launch of the building kernel from the ncu
-    summary committed under profiles/, or None when the summary is missing or
-    was taken on other kernel sources."""
-    path = os.path.join(ROOT, "profiles", "k_build_%s_ncu.md" % workload)
+def profiled_traffic(name, sources=KERNEL_SOURCES):
+    """DRAM bytes (read + write) per launch of a kernel from the ncu summary
+    profiles/<name>_ncu.md, or None when the summary is missing or was taken
+    on other kernel sources."""
+    path = os.path.join(ROOT, "profiles", "%s_ncu.md" % name)
     try:
         with open(path) as f:
             lines = f.read().splitlines()
@@ -487,7 +494,7 @@ def profiled_traffic(workload):
         if ln.startswith("kernel-source-sha1:") or ln.startswith("dram-bytes-per-launch:"):
             k, v = ln.split(":", 1)
             kv[k] = v.strip()
-    if kv.get("kernel-source-sha1") != kernel_digest() or "dram-bytes-per-launch" not in kv:
+    if kv.get("kernel-source-sha1") != kernel_digest(sources) or "dram-bytes-per-launch" not in kv:
         return None
     return int(kv["dram-bytes-per-launch"])
 
@@ -525,6 +532,12 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    if args.only:
+        import paper_2002_06295_gb300 as mkf_only
+        dev_only = torch.device("cuda", local)
+        fn = {"strips": measure_strips, "seeding": measure_seeding}[args.only]
+        print(json.dumps({args.only: fn(mkf_only, dev_only)}), flush=True)
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -765,7 +778,7 @@ def main():
         "work": stats,
         "roofline": {"kernel": "k_build (combinatorial building)", "bound": "alu", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": profiled_traffic(args.workload),
+                     "traffic": profiled_traffic("k_build_%s" % args.workload),
                      "peak_basis": "FP32: %d SMs x %d lanes x 2 x %.0f MHz" % (props.multi_processor_count,
                                                                                FP32_LANES, max_mhz),
                      "peak_fma_probe_tflops": fma_peak,

@@ -136,44 +136,44 @@ __device__ __forceinline__ float asin_over(float x) {
   return fabsf(x) < 1e-4f ? fmaf(x * x, 1.0f / 6.0f, 1.0f) : asinf(x) / x;
 }
 
-// Helix through the origin, a (layer 0, azimuth phia) and b (layer 1) if the
-// pair passes its cuts: its prediction on layer 2 (azimuth, direction, z).
-// One arcsine per radius serves both the path s(r) = r asin(u) / u (u = omega
-// r / 2) and the turning angle asin(u).
+// Pair cuts for the layer-0 hit a and a layer-1 hit b.  A passing pair keeps
+// what its layer-2 prediction needs: curvature w, g0 = asin(u0) / u0 (u0 = w
+// R0 / 2; s(R0) = R0 g0) and cot theta.
+struct PairCut {
+  bool ok;
+  float w, g0, cot;
+};
+__device__ __forceinline__ PairCut pair_cut(const SeedArgs& A, const SHit& a, const SHit& b) {
+  PairCut p{false, 0.f, 0.f, 0.f};
+  if (!(fmaf(a.c, b.c, a.s * b.s) > 0.f)) return p;   // opposite sides of the beam line
+  p.w = circle_origin(A.R[0], a, A.R[1], b);
+  if (!(fabsf(p.w) <= A.omega_max)) return p;
+  p.g0 = asin_over(0.5f * p.w * A.R[0]);
+  const float s0 = A.R[0] * p.g0;
+  p.cot = (b.z - a.z) / (A.R[1] * asin_over(0.5f * p.w * A.R[1]) - s0);
+  p.ok = fabsf(fmaf(-p.cot, s0, a.z)) <= A.z_max;
+  return p;
+}
+
+// Prediction on layer 2 of a passing pair (azimuth, direction, z): one more
+// arcsine serves both the path s(R2) = R2 asin(u2) / u2 and the turning angle.
 struct PairPred {
   bool ok;
   float phip, cp, sp, zp;
 };
-__device__ __forceinline__ PairPred pair_predict(const SeedArgs& A, const SHit& a, float phia, const SHit& b) {
-  PairPred q{false, 0.f, 0.f, 0.f, 0.f};
-  if (!(fmaf(a.c, b.c, a.s * b.s) > 0.f)) return q;   // opposite sides of the beam line
-  const float w = circle_origin(A.R[0], a, A.R[1], b);
-  if (!(fabsf(w) <= A.omega_max)) return q;
-  const float u0 = 0.5f * w * A.R[0], u1 = 0.5f * w * A.R[1], u2 = 0.5f * w * A.R[2];
-  const float g0 = asin_over(u0), g2 = asin_over(u2);
-  const float s0 = A.R[0] * g0;
-  const float cot = (b.z - a.z) / (A.R[1] * asin_over(u1) - s0);
-  const float z0 = fmaf(-cot, s0, a.z);
-  if (!(fabsf(z0) <= A.z_max)) return q;
-  const float d = fmaf(u2, g2, -u0 * g0);   // asin(u2) - asin(u0)
+__device__ __forceinline__ PairPred pair_predict(const SeedArgs& A, const SHit& a, float phia, const PairCut& p) {
+  PairPred q{true, 0.f, 0.f, 0.f, 0.f};
+  const float u0 = 0.5f * p.w * A.R[0], u2 = 0.5f * p.w * A.R[2];
+  const float g2 = asin_over(u2);
+  const float z0 = fmaf(-p.cot, A.R[0] * p.g0, a.z);
+  const float d = fmaf(u2, g2, -u0 * p.g0);   // asin(u2) - asin(u0)
   float sd, cd;
   sincosf(d, &sd, &cd);
   q.cp = fmaf(a.c, cd, -a.s * sd);
   q.sp = fmaf(a.s, cd, a.c * sd);
   q.phip = phia + d;
-  q.zp = fmaf(cot, A.R[2] * g2, z0);
-  q.ok = true;
+  q.zp = fmaf(p.cot, A.R[2] * g2, z0);
   return q;
-}
-
-// The pair cuts alone (what the layer-1 scan needs).
-__device__ __forceinline__ bool pair_passes(const SeedArgs& A, const SHit& a, const SHit& b) {
-  if (!(fmaf(a.c, b.c, a.s * b.s) > 0.f)) return false;
-  const float w = circle_origin(A.R[0], a, A.R[1], b);
-  if (!(fabsf(w) <= A.omega_max)) return false;
-  const float s0 = A.R[0] * asin_over(0.5f * w * A.R[0]);
-  const float cot = (b.z - a.z) / (A.R[1] * asin_over(0.5f * w * A.R[1]) - s0);
-  return fabsf(fmaf(-cot, s0, a.z)) <= A.z_max;
 }
 
 // Layer-2 hits that continue a passing pair: f(c, position) for each, in window order.
@@ -218,8 +218,8 @@ __global__ void __launch_bounds__(kSeedThreads)
                     const int* __restrict__ toff, int4* __restrict__ trip, unsigned long long* __restrict__ stats) {
   const int lane = threadIdx.x & 31;
   int st_l1 = 0, st_pairs = 0, st_l2 = 0, st_trip = 0;   // work counters (count pass; per lane)
-  __shared__ int queue_all[kSeedThreads / 32][64];   // per warp: passing pairs (layer-1 positions) in order
-  int* queue = queue_all[threadIdx.x >> 5];
+  __shared__ int4 queue_all[kSeedThreads / 32][64];   // per warp: passing pairs in order (layer-1 position, w, g0, cot)
+  int4* queue = queue_all[threadIdx.x >> 5];
   const int64_t B = A.bins_per_event;
   const int n_items = __ldg(&l0_cum[A.n_events]);
   const int64_t n_warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -250,15 +250,18 @@ __global__ void __launch_bounds__(kSeedThreads)
     int queued = 0;   // passing pairs waiting in the warp's queue (uniform)
     // the first `cnt` queued pairs, one per lane, search their layer-2 windows
     auto drain = [&](int cnt) {
-      const int pb = lane < cnt ? queue[lane] : -1;
+      const bool have = lane < cnt;
+      const int pb = have ? queue[lane].x : -1;
+      const PairCut pc{have, have ? __int_as_float(queue[lane].y) : 0.f, have ? __int_as_float(queue[lane].z) : 0.f,
+                       have ? __int_as_float(queue[lane].w) : 0.f};
       __syncwarp();
       for (int j = lane; j + 32 < queued; j += 32) queue[j] = queue[j + 32];   // keep the rest in order
       __syncwarp();
       int mine = 0;
       PairPred q{false, 0.f, 0.f, 0.f, 0.f};
-      if (pb >= 0) {
-        q = pair_predict(A, a, phia, load_shit(rec, pb));
-        if (q.ok) for_layer2(A, ebase, q, bin_off, rec, st_l2, [&](const SHit&, int) { ++mine; });
+      if (have) {
+        q = pair_predict(A, a, phia, pc);
+        for_layer2(A, ebase, q, bin_off, rec, st_l2, [&](const SHit&, int) { ++mine; });
       }
       int ex = mine;   // prefix of the lanes' triplet counts
 #pragma unroll
@@ -272,7 +275,7 @@ __global__ void __launch_bounds__(kSeedThreads)
         int64_t i = base + n + ex;
         int unused = 0;
         for_layer2(A, ebase, q, bin_off, rec, unused,
-                   [&](const SHit&, int pc) { trip[i++] = make_int4(pos, pb, pc, ebase); });
+                   [&](const SHit&, int pcpos) { trip[i++] = make_int4(pos, pb, pcpos, ebase); });
       }
       n += group;
       queued -= cnt;
@@ -297,11 +300,13 @@ __global__ void __launch_bounds__(kSeedThreads)
         const int rx = __shfl_sync(0xFFFFFFFFu, r.x, row);
         const int pre = __shfl_sync(0xFFFFFFFFu, incl - len, row);
         const int pb = t < tot ? rx + (t - pre) : -1;
-        const bool pass = pb >= 0 && pair_passes(A, a, load_shit(rec, pb));
-        const unsigned m = __ballot_sync(0xFFFFFFFFu, pass);
+        const PairCut pc = pb >= 0 ? pair_cut(A, a, load_shit(rec, pb)) : PairCut{false, 0.f, 0.f, 0.f};
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, pc.ok);
         st_l1 += pb >= 0;
-        st_pairs += pass;
-        if (pass) queue[queued + __popc(m & ((1u << lane) - 1u))] = pb;   // append in order
+        st_pairs += pc.ok;
+        if (pc.ok)   // append in order
+          queue[queued + __popc(m & ((1u << lane) - 1u))] =
+              make_int4(pb, __float_as_int(pc.w), __float_as_int(pc.g0), __float_as_int(pc.cot));
         __syncwarp();
         queued += __popc(m);
         if (queued >= 32) drain(32);
