@@ -79,6 +79,9 @@ def lib():
             L.orc_seed_quads.argtypes = [P, P, ctypes.c_longlong, P, c_int, P, P, c_double, c_double, c_double,
                                          c_double, c_double, c_double, ctypes.c_longlong, P, P, P, P]
             L.orc_seed_quads.restype = ctypes.c_longlong
+            L.orc_overlaps.argtypes = [P, c_int, c_double, P, P, P, c_int, P, c_int, P, c_int, P, P, c_int,
+                                       c_double, P, P, P, P]
+            L.orc_overlaps.restype = c_int
             _lib = L
     return _lib
 
@@ -236,6 +239,27 @@ def fit_grad(geo, hit_xyz, hit_lcov, hit_layer, hits, init_par, init_cov, g_chi2
                        _pd(ic), int(T), _pd(al), _pd(xx), _pd(_d(g_chi2)), _pd(gp), _pd(gc), _pd(gh), _pd(ga),
                        _pd(gx))
     return gh, ga, gx
+
+
+def overlaps(geo, hit_xyz, hit_lcov, hit_layer, hits, init_par, init_cov, ev_hit_off=None, chi2_cut=20.0):
+    """Overlap-hit recovery (a second hit on the layer of each track hit, best
+    predicted chi2 against the fitted state after that hit, below chi2_cut).
+    hits [T, K] global ids; init_par [T, 6], init_cov [T, 21].  Returns dict
+    hit [T, K] (-1: none), chi2, gap (relative chi2 gap to the runner-up) and
+    best (best candidate chi2, passing or not)."""
+    hx, hc, hl = _d(hit_xyz), _d(hit_lcov), _i(hit_layer)
+    h = _i(hits)
+    T, K = h.shape
+    H = int(hl.shape[0])
+    off = np.ascontiguousarray([0, H] if ev_hit_off is None else ev_hit_off, np.int64)
+    ip, ic = _d(init_par), _d(init_cov)
+    out = {"hit": np.zeros((T, K), np.int32), "chi2": np.zeros((T, K)), "gap": np.zeros((T, K)),
+           "best": np.zeros((T, K))}
+    lib().orc_overlaps(geo.table.ctypes.data, geo.L, geo.bz, hx.ctypes.data, hc.ctypes.data, hl.ctypes.data, H,
+                       off.ctypes.data, off.size - 1, h.ctypes.data, int(K), ip.ctypes.data, ic.ctypes.data, int(T),
+                       float(chi2_cut), out["hit"].ctypes.data, out["chi2"].ctypes.data, out["gap"].ctypes.data,
+                       out["best"].ctypes.data)
+    return out
 
 
 def strip_clusters(adc, noise_q, bad, max_bad_gap=1, q_min=30):

@@ -881,6 +881,80 @@ int orc_fit(const double* layers, int L, double bz, const double* hit_xyz, const
   return 0;
 }
 
+// Overlap-hit recovery (Sec. 3: hits in overlapping detector modules, more
+// than one hit per layer assigned to a track; the paper plans the feature and
+// fixes no rule, so this is a reading): run the forward fit of each track;
+// after the update with its hit h on layer l, every other hit of the same
+// event on layer l in the state's half plane is a candidate, with the
+// predicted chi2 of that hit against the updated state (the state is not
+// updated with it); the overlap hit is the candidate of smallest chi2 below
+// chi2_cut (ties: smaller id).  Outputs per (track, slot): out_hit (-1:
+// none), out_chi2, and for comparisons out_gap = the relative chi2 gap from
+// the best candidate to the next one (inf if none) and out_best = the best
+// candidate's chi2 whether or not it passes the cut (inf if none).
+int orc_overlaps(const double* layers, int L, double bz, const double* hit_xyz, const double* hit_lcov,
+                 const int* hit_layer, int H, const long long* ev_hit_off, int n_events, const int* hits, int K,
+                 const double* init_par, const double* init_cov, int T, double chi2_cut, int* out_hit,
+                 double* out_chi2, double* out_gap, double* out_best) {
+  Geom g = make_geom(layers, L, bz);
+  FitInputs<double> in{&g, hit_xyz, hit_lcov, hit_layer, nullptr, nullptr};
+  for (int t = 0; t < T; ++t) {
+    const int* ids = hits + (size_t)t * K;
+    for (int k = 0; k < K; ++k) {
+      out_hit[(size_t)t * K + k] = -1;
+      out_chi2[(size_t)t * K + k] = 0.0;
+      out_gap[(size_t)t * K + k] = INFINITY;
+      out_best[(size_t)t * K + k] = INFINITY;
+    }
+    int first = -1;
+    for (int k = 0; k < K && first < 0; ++k) first = ids[k];
+    if (first < 0) continue;
+    int e = 0;   // the track's event: the one holding its first hit
+    while (e + 1 < n_events && ev_hit_off[e + 1] <= first) ++e;
+    double p[6], C[21];
+    for (int k = 0; k < 6; ++k) p[k] = init_par[6 * t + k];
+    for (int k = 0; k < 21; ++k) C[k] = init_cov[21 * t + k];
+    for (int k = 0; k < K; ++k) {
+      const int h = ids[k];
+      if (h < 0) continue;
+      const int l = hit_layer[h];
+      Surf<double> sf = fit_surf(in, l);
+      double pp[6], CC[21];
+      if (!transport(p, C, sf, g.bz, +1, pp, CC, (double*)nullptr)) break;
+      add_material(pp, sf, CC);
+      kf_update(pp, CC, fit_meas(in, h), true);
+      for (int i = 0; i < 6; ++i) p[i] = pp[i];
+      for (int i = 0; i < 21; ++i) C[i] = CC[i];
+      double best = INFINITY, second = INFINITY;
+      int best_id = -1;
+      for (long long h2 = ev_hit_off[e]; h2 < ev_hit_off[e + 1]; ++h2) {
+        if (h2 == h || hit_layer[h2] != l) continue;
+        const Meas<double> m2 = fit_meas(in, (int)h2);
+        if (!same_side(p, m2)) continue;
+        double q[6], Q[21];
+        for (int i = 0; i < 6; ++i) q[i] = p[i];
+        for (int i = 0; i < 21; ++i) Q[i] = C[i];
+        const double c2 = kf_update(q, Q, m2, false);
+        if (c2 < best) {
+          second = best;
+          best = c2;
+          best_id = (int)h2;
+        } else if (c2 < second) {
+          second = c2;
+        }
+      }
+      const size_t o = (size_t)t * K + k;
+      out_best[o] = best;
+      out_gap[o] = best_id >= 0 ? (second - best) / std::max(1.0, best) : INFINITY;
+      if (best_id >= 0 && best < chi2_cut) {
+        out_hit[o] = best_id;
+        out_chi2[o] = best;
+      }
+    }
+  }
+  return 0;
+}
+
 // Reference gradient of the forward fit, by forward-mode dual numbers (one
 // pass per input direction):  loss = sum_t g_chi2[t] chi2_t + g_par[t].p_t +
 // g_cov[t].C_t (packed entries); returns d loss / d hit xyz [H][3],

@@ -44,6 +44,7 @@ class Event:
     true_hits: np.ndarray     # [S, L] int32 hit ids in crossing order, -1 padded
     true_layers: np.ndarray   # [S, L] int32 crossed layer ids, -1 padded
     true_state: np.ndarray = None   # [S, L, 6] at each crossing: position, kappa, direction after the kick
+    true_overlap: np.ndarray = None   # [S, L] int32 second hit of each crossing (overlapping module), -1 if none
 
     @property
     def n_hits(self):
@@ -126,7 +127,11 @@ def _highland(t_eff, kappa, theta):
 
 def simulate_event(geom: Geometry, n_tracks: int, rng: np.random.Generator, *,
                    pt_range=(0.5, 10.0), pt_log=False, eta_max=1.0, noise_frac=0.0,
-                   seed_smear=0.05, kick=True):
+                   seed_smear=0.05, kick=True, overlap_frac=0.0):
+    """overlap_frac: probability that a barrel crossing also leaves a second,
+    independently smeared hit on the same layer (a stand-in for the track
+    passing through two overlapping modules; the collapsed layer puts both on
+    its radius).  With 0 no extra random numbers are drawn."""
     L = geom.n_layers
     T = n_tracks
     r_max = tracking_radius(geom)
@@ -151,6 +156,9 @@ def simulate_event(geom: Geometry, n_tracks: int, rng: np.random.Generator, *,
     cross_layer = np.full((T, L), -1, np.int32)
     cross_hit = np.full((T, L), -1, np.int64)     # provisional index into the signal list
     cross_state = np.full((T, L, 6), np.nan)
+    cross_over = np.full((T, L), -1, np.int64)    # provisional index into the overlap list
+    ox, oy, oz, ol, ot, oa, ob = [], [], [], [], [], [], []
+    n_over = 0
     n_cross = np.zeros(T, np.int64)
     n_sig = 0
     for _ in range(L):
@@ -220,6 +228,19 @@ def simulate_event(geom: Geometry, n_tracks: int, rng: np.random.Generator, *,
         cross_hit[idx, k] = n_sig + np.arange(idx.size)
         n_cross[idx] += 1
         n_sig += idx.size
+        if overlap_frac > 0.0:   # a second hit from an overlapping module
+            sel = barrel & (rng.random(idx.size) < overlap_frac)
+            ns = int(sel.sum())
+            if ns:
+                ga2 = rng.standard_normal(ns)
+                gb2 = rng.standard_normal(ns)
+                r2 = geom.pos[nxt[sel]]
+                ph2 = phic[sel] + ga2 * sa[sel] / r2
+                ox.append(r2 * np.cos(ph2)); oy.append(r2 * np.sin(ph2)); oz.append(nz[sel] + gb2 * sb[sel])
+                ol.append(nxt[sel].astype(np.int32)); ot.append(idx[sel].astype(np.int32))
+                oa.append(sa[sel] ** 2); ob.append(sb[sel] ** 2)
+                cross_over[idx[sel], k[sel]] = n_over + np.arange(ns)
+                n_over += ns
         # multiple-scattering kick after the crossing
         if kick:
             cosinc = np.where(barrel, np.sin(ts) * (nx * np.cos(nphi) + ny * np.sin(nphi)) / rc,
@@ -233,9 +254,9 @@ def simulate_event(geom: Geometry, n_tracks: int, rng: np.random.Generator, *,
         cross_state[idx, k] = np.stack([nx, ny, nz, kappa[idx], phi[idx], theta[idx]], 1)
 
     if n_sig:
-        sx = np.concatenate(hx); sy = np.concatenate(hy); sz = np.concatenate(hz)
-        sl = np.concatenate(hl); st = np.concatenate(ht)
-        sva = np.concatenate(ha); svb = np.concatenate(hb)
+        sx = np.concatenate(hx + ox); sy = np.concatenate(hy + oy); sz = np.concatenate(hz + oz)
+        sl = np.concatenate(hl + ol); st = np.concatenate(ht + ot)
+        sva = np.concatenate(ha + oa); svb = np.concatenate(hb + ob)
     else:
         sx = sy = sz = sva = svb = np.zeros(0)
         sl = st = np.zeros(0, np.int32)
@@ -270,6 +291,7 @@ def simulate_event(geom: Geometry, n_tracks: int, rng: np.random.Generator, *,
     hit_layer = sl[perm].astype(np.int32)
     hit_track = st[perm].astype(np.int32)
     true_hits = np.where(cross_hit >= 0, inv[np.maximum(cross_hit, 0)], -1).astype(np.int32)
+    true_overlap = np.where(cross_over >= 0, inv[np.maximum(n_sig + cross_over, 0)], -1).astype(np.int32)
 
     # seeds: true vertex parameters smeared by 5 %
     ks = kappa * (1.0 + seed_smear * rng.standard_normal(T))
@@ -282,7 +304,7 @@ def simulate_event(geom: Geometry, n_tracks: int, rng: np.random.Generator, *,
         seed_cov[:, cov_index(i, i)] = (seed_smear * ks) ** 2 if i == 3 else diag[i]
     return Event(geom=geom, hit_xyz=hit_xyz, hit_lcov=hit_lcov, hit_layer=hit_layer,
                  hit_track=hit_track, seed_par=seed_par, seed_cov=seed_cov, true_par=true_par,
-                 true_hits=true_hits, true_layers=cross_layer, true_state=cross_state)
+                 true_hits=true_hits, true_layers=cross_layer, true_state=cross_state, true_overlap=true_overlap)
 
 
 # ---------------------------------------------------------------------------
@@ -316,12 +338,12 @@ def _n_tracks(spec, rng):
     return int(t)
 
 
-def make_config_event(config: int, event: int = 0, n_tracks=None) -> Event:
+def make_config_event(config: int, event: int = 0, n_tracks=None, overlap_frac=0.0) -> Event:
     spec = CONFIGS[config]
     rng = np.random.default_rng(config_seed(config, event))
     n = _n_tracks(spec, rng) if n_tracks is None else int(n_tracks)
     return simulate_event(spec["geom"](), n, rng, pt_range=spec["pt_range"], pt_log=spec["pt_log"],
-                          eta_max=spec["eta_max"], noise_frac=spec["noise_frac"])
+                          eta_max=spec["eta_max"], noise_frac=spec["noise_frac"], overlap_frac=overlap_frac)
 
 
 def make_batch(config: int, n_events=None, n_tracks=None) -> EventBatch:
