@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c5"],
                     help="timed workload (c2: the CMS-like event the metric is quoted on)")
     ap.add_argument("--no-graph", action="store_true", help="time eager launches only (no CUDA-graph replay)")
-    ap.add_argument("--only", choices=["strips", "seeding"],
+    ap.add_argument("--only", choices=["strips", "seeding", "overlaps"],
                     help="run one secondary measurement alone and print it (for profiling its kernel)")
     return ap.parse_args()
 
@@ -461,6 +461,68 @@ def measure_seeding(mkf, dev, reps=5):
                              "oracle_seeds": int(ref["hits"].shape[0])}}
 
 
+def measure_overlaps(mkf, dev, reps=5):
+    """Overlap-hit recovery on the C2 event with overlapping modules (30 % of
+    barrel crossings leave a second hit): build, then time mkf_find_overlaps
+    over the built tracks; recovery against the simulation's truth; FP32
+    roofline of its work (the fit steps and chi2 of the building kernel's
+    formulas); the oracle on a sample of tracks on one core."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import synth.events as sev
+    ev = sev.make_config_event(2, overlap_frac=0.3)
+    ctx = mkf.Context(dev.index)
+    mkf.mkf_load_geometry(ctx, ev.geom.table(), ev.geom.bz, 64, 16)
+    t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(dev, dt)
+    xyz, lcov, lay = t(ev.hit_xyz.T, torch.float32), t(ev.hit_lcov.T, torch.float32), t(ev.hit_layer, torch.int32)
+    mkf.mkf_bin_hits(ctx, xyz, lcov, lay, t(np.array([0, ev.n_hits]), torch.int64))
+    sp, sc = t(ev.seed_par.T, torch.float32), t(ev.seed_cov.T, torch.float32)
+    b = mkf.mkf_build_tracks(ctx, sp, sc, t(np.array([0, ev.n_seeds]), torch.int64), chi2_cut=30.0, max_cands=6,
+                             max_holes=3, min_hits=4, dup_frac=0.5)
+    o = mkf.mkf_find_overlaps(ctx, xyz, lcov, lay, b["hits"], sp, sc)
+    stream = torch.cuda.current_stream()
+    ts = []
+    for r in range(reps + 1):
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        mkf.mkf_find_overlaps(ctx, xyz, lcov, lay, b["hits"], sp, sc, out=o)
+        e.record(stream)
+        e.synchronize()
+        if r:
+            ts.append(a.elapsed_time(e))
+    mkf.mkf_sync(ctx)
+    w = mkf.mkf_get_overlap_stats(ctx)
+    fma_peak = mkf.mkf_measure_fp32_peak(ctx)
+    bh, flags, gh = b["hits"].cpu().numpy(), b["flags"].cpu().numpy(), o["hit"].cpu().numpy()
+    ctx.close()
+    ok = tot = 0
+    for tr in np.nonzero(flags == mkf.TRK_KEPT)[0]:
+        truth = {int(h): k for k, h in enumerate(ev.true_hits[tr]) if h >= 0}
+        for k, h in enumerate(bh[tr]):
+            if h >= 0 and int(h) in truth and ev.true_overlap[tr, truth[int(h)]] >= 0:
+                tot += 1
+                ok += gh[tr, k] == ev.true_overlap[tr, truth[int(h)]]
+    ms = min(ts)
+    flops = w["hits_fitted"] * (FLOPS_CAND_STEP + FLOPS_UPDATE) + w["candidates"] * (FLOPS_BOX + FLOPS_CHI2)
+    ach = flops / (ms * 1e-3) / 1e12
+    n_s = 500
+    t0 = time.perf_counter()
+    oracle.overlaps(oracle.Geo.of(ev.geom), ev.hit_xyz, ev.hit_lcov, ev.hit_layer, bh[:n_s], ev.seed_par[:n_s],
+                    ev.seed_cov[:n_s])
+    cpu_s = time.perf_counter() - t0
+    return {"workload": "C2 event with overlapping modules (30 %% of barrel crossings leave a second hit): %d hits, "
+                        "%d built tracks; chi2 < 20, box 1 cm (r phi) x 10 cm" % (ev.n_hits, ev.n_seeds),
+            "ms": ms, "tracks_per_s": ev.n_seeds / (ms * 1e-3), "work": w,
+            "recovered_true_overlaps": ok / tot if tot else None, "true_overlaps_on_kept_tracks": tot,
+            "roofline": {"bound": "alu", "achieved": ach, "peak": fma_peak, "unit": "TFLOP/s",
+                         "frac": ach / fma_peak if fma_peak else None,
+                         "peak_basis": "FP32 FMA probe on this device (mkf_measure_fp32_peak)"},
+            "cpu_baseline": {"value": n_s / cpu_s, "unit": "tracks/s", "cores": 1, "kind": "oracle",
+                             "sample": "the first %d built tracks (brute force over the layer's hits)" % n_s}}
+
+
 KERNEL_SOURCES = ("paper_2002_06295_gb300/csrc/build.cu", "paper_2002_06295_gb300/csrc/mkf_device.cuh",
                   "paper_2002_06295_gb300/csrc/mkf_internal.h")
 STRIP_SOURCES = ("paper_2002_06295_gb300/csrc/strips.cu", "paper_2002_06295_gb300/csrc/mkf_internal.h")
@@ -535,7 +597,7 @@ def main():
     if args.only:
         import paper_2002_06295_gb300 as mkf_only
         dev_only = torch.device("cuda", local)
-        fn = {"strips": measure_strips, "seeding": measure_seeding}[args.only]
+        fn = {"strips": measure_strips, "seeding": measure_seeding, "overlaps": measure_overlaps}[args.only]
         print(json.dumps({args.only: fn(mkf_only, dev_only)}), flush=True)
         return
     dist = None
@@ -746,7 +808,8 @@ def main():
         secondary = {"batched_vs_plain": measure_batched(mkf, _tune, dev),
                      "fit_gradient": measure_fit_gradient(mkf, dev),
                      "strip_clustering": measure_strips(mkf, dev),
-                     "seeding": measure_seeding(mkf, dev)}
+                     "seeding": measure_seeding(mkf, dev),
+                     "overlaps": measure_overlaps(mkf, dev)}
     value = units * args.steps / (total_ms * 1e-3)
     e2e_value = units * args.steps / (e2e_total * 1e-3)
     b_ms = statistics.mean(build_ms)

@@ -183,6 +183,32 @@ mkf_status mkf_seed_tracks(mkf_ctx* ctx, float pt_min, float z_max, float rphi_t
  * HOST output of n <= 6 values (zeros before the first call). */
 mkf_status mkf_get_seed_stats(mkf_ctx* ctx, int64_t* out, int n, void* stream);
 
+/* Recovery of hits in overlapping detector modules (Sec. 3: more than one hit
+ * per layer assigned to a track; the paper plans the feature without a rule,
+ * so this is the library's reading).  For each track the forward fit of
+ * mkf_fit_tracks runs over its hits (same steps, FP32); after the update with
+ * its hit h on layer l, the overlap hit of that crossing is the other hit of
+ * layer l (in h's event, among the binned hits of the last mkf_bin_hits, which
+ * must be these hits) inside the adjacent-module box around h -- |R sin(phi -
+ * phi_h)| <= max_drphi with cos > 0 (R the layer radius on a barrel, h's
+ * radius on a disk) and |w - w_h| <= max_dw (w = z on a barrel, r on a disk),
+ * in cm -- with the smallest predicted chi2 against the updated state, if
+ * below chi2_cut (ties: smaller id).  The state is not updated with
+ * it.  Inputs as for mkf_fit_tracks (no alignment or thickness override).
+ * Outputs (DEVICE): out_hit [T][K] caller hit id or -1 for each slot,
+ * out_chi2 [T][K] its chi2 (0 when none).  Slots after a surface that is not
+ * reached stay -1.  MKF_ERR_STATE without geometry or binned hits,
+ * MKF_ERR_ARG if n_hits differs from the binned hits. */
+mkf_status mkf_find_overlaps(mkf_ctx* ctx, const float* xyz, const float* lcov, const int* layer, int64_t n_hits,
+                             const int* hits, int K, const float* init_par, const float* init_cov, int64_t n_tracks,
+                             float chi2_cut, float max_drphi, float max_dw, int* out_hit, float* out_chi2,
+                             void* stream);
+
+/* Work counters of the last mkf_find_overlaps (synchronises `stream`): [0]
+ * track hits fitted, [1] candidate hits whose chi2 was evaluated, [2] overlap
+ * hits found.  HOST output of n <= 3 values. */
+mkf_status mkf_get_overlap_stats(mkf_ctx* ctx, int64_t* out, int n, void* stream);
+
 /* Read back the binning (for inspection and tests): perm [H] original id of
  * each sorted position, bin_off [n_bins_total+1] first sorted position of each
  * (event, layer, bin), n_bins_total = n_events * sum_l(n_phi_l * n_w_l).

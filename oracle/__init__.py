@@ -80,7 +80,7 @@ def lib():
                                          c_double, c_double, c_double, ctypes.c_longlong, P, P, P, P]
             L.orc_seed_quads.restype = ctypes.c_longlong
             L.orc_overlaps.argtypes = [P, c_int, c_double, P, P, P, c_int, P, c_int, P, c_int, P, P, c_int,
-                                       c_double, P, P, P, P]
+                                       c_double, c_double, c_double, P, P, P, P]
             L.orc_overlaps.restype = c_int
             _lib = L
     return _lib
@@ -241,9 +241,12 @@ def fit_grad(geo, hit_xyz, hit_lcov, hit_layer, hits, init_par, init_cov, g_chi2
     return gh, ga, gx
 
 
-def overlaps(geo, hit_xyz, hit_lcov, hit_layer, hits, init_par, init_cov, ev_hit_off=None, chi2_cut=20.0):
-    """Overlap-hit recovery (a second hit on the layer of each track hit, best
-    predicted chi2 against the fitted state after that hit, below chi2_cut).
+def overlaps(geo, hit_xyz, hit_lcov, hit_layer, hits, init_par, init_cov, ev_hit_off=None, chi2_cut=20.0,
+             max_drphi=1.0, max_dw=10.0):
+    """Overlap-hit recovery (a second hit on the layer of each track hit, in
+    the adjacent-module box |d(r phi)| <= max_drphi, |dw| <= max_dw around it,
+    best predicted chi2 against the fitted state after that hit, below
+    chi2_cut).
     hits [T, K] global ids; init_par [T, 6], init_cov [T, 21].  Returns dict
     hit [T, K] (-1: none), chi2, gap (relative chi2 gap to the runner-up) and
     best (best candidate chi2, passing or not)."""
@@ -257,7 +260,8 @@ def overlaps(geo, hit_xyz, hit_lcov, hit_layer, hits, init_par, init_cov, ev_hit
            "best": np.zeros((T, K))}
     lib().orc_overlaps(geo.table.ctypes.data, geo.L, geo.bz, hx.ctypes.data, hc.ctypes.data, hl.ctypes.data, H,
                        off.ctypes.data, off.size - 1, h.ctypes.data, int(K), ip.ctypes.data, ic.ctypes.data, int(T),
-                       float(chi2_cut), out["hit"].ctypes.data, out["chi2"].ctypes.data, out["gap"].ctypes.data,
+                       float(chi2_cut), float(max_drphi), float(max_dw), out["hit"].ctypes.data,
+                       out["chi2"].ctypes.data, out["gap"].ctypes.data,
                        out["best"].ctypes.data)
     return out
 

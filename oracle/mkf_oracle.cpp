@@ -885,7 +885,10 @@ int orc_fit(const double* layers, int L, double bz, const double* hit_xyz, const
 // than one hit per layer assigned to a track; the paper plans the feature and
 // fixes no rule, so this is a reading): run the forward fit of each track;
 // after the update with its hit h on layer l, every other hit of the same
-// event on layer l in the state's half plane is a candidate, with the
+// event on layer l in the state's half plane that lies in the adjacent-module
+// box around h (|R sin(phi_2 - phi_h)| <= max_drphi with cos > 0, R the layer
+// radius on a barrel or h's radius on a disk, and |w_2 - w_h| <= max_dw, w = z
+// on a barrel, r on a disk) is a candidate, with the
 // predicted chi2 of that hit against the updated state (the state is not
 // updated with it); the overlap hit is the candidate of smallest chi2 below
 // chi2_cut (ties: smaller id).  Outputs per (track, slot): out_hit (-1:
@@ -894,8 +897,8 @@ int orc_fit(const double* layers, int L, double bz, const double* hit_xyz, const
 // candidate's chi2 whether or not it passes the cut (inf if none).
 int orc_overlaps(const double* layers, int L, double bz, const double* hit_xyz, const double* hit_lcov,
                  const int* hit_layer, int H, const long long* ev_hit_off, int n_events, const int* hits, int K,
-                 const double* init_par, const double* init_cov, int T, double chi2_cut, int* out_hit,
-                 double* out_chi2, double* out_gap, double* out_best) {
+                 const double* init_par, const double* init_cov, int T, double chi2_cut, double max_drphi,
+                 double max_dw, int* out_hit, double* out_chi2, double* out_gap, double* out_best) {
   Geom g = make_geom(layers, L, bz);
   FitInputs<double> in{&g, hit_xyz, hit_lcov, hit_layer, nullptr, nullptr};
   for (int t = 0; t < T; ++t) {
@@ -927,9 +930,13 @@ int orc_overlaps(const double* layers, int L, double bz, const double* hit_xyz, 
       for (int i = 0; i < 21; ++i) C[i] = CC[i];
       double best = INFINITY, second = INFINITY;
       int best_id = -1;
+      const Meas<double> mh = fit_meas(in, h);
+      const double Rh = g.layers[l].kind == 0 ? g.layers[l].pos : mh.w;
       for (long long h2 = ev_hit_off[e]; h2 < ev_hit_off[e + 1]; ++h2) {
         if (h2 == h || hit_layer[h2] != l) continue;
         const Meas<double> m2 = fit_meas(in, (int)h2);
+        const double cd = mh.c * m2.c + mh.s * m2.s, sd = mh.c * m2.s - mh.s * m2.c;
+        if (!(cd > 0.0) || std::fabs(Rh * sd) > max_drphi || std::fabs(m2.w - mh.w) > max_dw) continue;
         if (!same_side(p, m2)) continue;
         double q[6], Q[21];
         for (int i = 0; i < 6; ++i) q[i] = p[i];

@@ -258,6 +258,35 @@ def mkf_seed_tracks(ctx, pt_min=0.5, z_max=5.0, rphi_tol=0.05, z_tol=0.1, max_se
     return res
 
 
+def mkf_find_overlaps(ctx, xyz, lcov, layer, hits, init_par, init_cov, chi2_cut=20.0, max_drphi=1.0, max_dw=10.0,
+                      out=None, stream=None):
+    """Overlap hits of tracks (hits [T, K] int32, init_par [6, T], init_cov
+    [21, T]); xyz, lcov, layer as for mkf_bin_hits (the binned hits).
+    Returns dict hit [T, K] int32 (-1: none) and chi2 [T, K] (device)."""
+    T, K = int(hits.shape[0]), int(hits.shape[1])
+    H = int(layer.shape[0])
+    dev = hits.device
+    o = out or dict(hit=torch.empty((T, K), dtype=torch.int32, device=dev),
+                    chi2=torch.empty((T, K), dtype=torch.float32, device=dev))
+    ctx._check(ctx.lib.mkf_find_overlaps(ctx.h, _ptr(xyz, torch.float32, "xyz"), _ptr(lcov, torch.float32, "lcov"),
+                                         _ptr(layer, torch.int32, "layer"), H, _ptr(hits, torch.int32, "hits"), K,
+                                         _ptr(init_par, torch.float32, "init_par"),
+                                         _ptr(init_cov, torch.float32, "init_cov"), T, float(chi2_cut),
+                                         float(max_drphi), float(max_dw), _ptr(o["hit"]), _ptr(o["chi2"]),
+                                         _stream(stream)), "mkf_find_overlaps")
+    return o
+
+
+OVERLAP_STAT_NAMES = ("hits_fitted", "candidates", "found")
+
+
+def mkf_get_overlap_stats(ctx, stream=None):
+    buf = (ctypes.c_int64 * len(OVERLAP_STAT_NAMES))()
+    ctx._check(ctx.lib.mkf_get_overlap_stats(ctx.h, ctypes.cast(buf, ctypes.c_void_p), len(OVERLAP_STAT_NAMES),
+                                             _stream(stream)), "mkf_get_overlap_stats")
+    return {k: int(buf[i]) for i, k in enumerate(OVERLAP_STAT_NAMES)}
+
+
 SEED_STAT_NAMES = ("l1_examined", "pairs", "l2_examined", "triplets", "l3_examined", "seeds")
 
 

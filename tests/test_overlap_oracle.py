@@ -6,7 +6,8 @@ from its selection code:
     after it (computed here in numpy from the fit oracle's state);
   * hits on other layers, in other events, on the far side of the axis, or
     the track's own hit are never chosen; of two identical copies the smaller
-    id is; the chi2 cut is strict;
+    id is; the chi2 cut is strict; a candidate just outside the
+    adjacent-module box is not taken, one just inside is;
   * on simulated events with overlapping modules, the simulation's own overlap
     hits are found for more than 95 % of the crossings that have one, and
     fewer than 5 % of the crossings without one get a hit."""
@@ -108,6 +109,35 @@ def test_never_other_layers_events_far_side_or_itself():
     hk = np.where((hits >= 0) & (hk < 0), -1, hk)
     r3 = oracle.overlaps(geo, ev.hit_xyz[keep], ev.hit_lcov[keep], ev.hit_layer[keep], hk, par, cov, chi2_cut=1e9)
     assert r3["hit"][t, k] == -1 and np.isinf(r3["best"][t, k])
+
+
+def test_adjacent_module_box():
+    """With hit variances so large that chi2 cannot decide, the box does: a
+    copy of the hit turned by just under max_drphi / R about the axis is taken,
+    just over is not; the same in z with max_dw."""
+    ev = sev.make_config_event(1, n_tracks=60)
+    geo = oracle.Geo.of(ev.geom)
+    hits, par, cov = _tracks(ev, 3)
+    t, k = 0, 3
+    h = hits[t, k]
+    R = ev.geom.pos[ev.hit_layer[h]]
+    lcov = ev.hit_lcov.copy()
+    lcov[:, 0] = lcov[:, 1] = 100.0   # 10 cm resolution: every nearby hit has a tiny chi2
+    H = ev.n_hits
+    for f, taken in ((0.99, True), (1.01, False)):
+        d = f * 1.0 / R
+        x, y, z = ev.hit_xyz[h]
+        c = np.array([[x * np.cos(d) - y * np.sin(d), x * np.sin(d) + y * np.cos(d), z]])
+        r = oracle.overlaps(geo, np.concatenate([ev.hit_xyz, c]), np.concatenate([lcov, lcov[h:h + 1]]),
+                            np.concatenate([ev.hit_layer, ev.hit_layer[h:h + 1]]), hits, par, cov, chi2_cut=1e9,
+                            max_drphi=1.0, max_dw=10.0)
+        assert (r["hit"][t, k] == H) == taken, f
+    for dz, taken in ((9.9, True), (10.1, False)):
+        c = ev.hit_xyz[h:h + 1] + np.array([[0.0, 0.0, dz]])
+        r = oracle.overlaps(geo, np.concatenate([ev.hit_xyz, c]), np.concatenate([lcov, lcov[h:h + 1]]),
+                            np.concatenate([ev.hit_layer, ev.hit_layer[h:h + 1]]), hits, par, cov, chi2_cut=1e9,
+                            max_drphi=1.0, max_dw=10.0)
+        assert (r["hit"][t, k] == H) == taken, dz
 
 
 def test_simulated_overlaps_are_recovered():
