@@ -518,16 +518,19 @@ def measure_overlaps(mkf, dev, reps=5):
             "recovered_true_overlaps": ok / tot if tot else None, "true_overlaps_on_kept_tracks": tot,
             "roofline": {"bound": "alu", "achieved": ach, "peak": fma_peak, "unit": "TFLOP/s",
                          "frac": ach / fma_peak if fma_peak else None,
+                         "traffic": profiled_traffic("k_overlaps", OVERLAP_SOURCES),
                          "peak_basis": "FP32 FMA probe on this device (mkf_measure_fp32_peak)"},
             "cpu_baseline": {"value": n_s / cpu_s, "unit": "tracks/s", "cores": 1, "kind": "oracle",
                              "sample": "the first %d built tracks (brute force over the layer's hits)" % n_s}}
 
 
 KERNEL_SOURCES = ("paper_2002_06295_gb300/csrc/build.cu", "paper_2002_06295_gb300/csrc/mkf_device.cuh",
-                  "paper_2002_06295_gb300/csrc/mkf_internal.h")
-STRIP_SOURCES = ("paper_2002_06295_gb300/csrc/strips.cu", "paper_2002_06295_gb300/csrc/mkf_internal.h")
+                  "paper_2002_06295_gb300/csrc/mkf_geom.h")
+STRIP_SOURCES = ("paper_2002_06295_gb300/csrc/strips.cu", "paper_2002_06295_gb300/csrc/mkf_geom.h")
 SEED_SOURCES = ("paper_2002_06295_gb300/csrc/seeds.cu", "paper_2002_06295_gb300/csrc/mkf_device.cuh",
-                "paper_2002_06295_gb300/csrc/mkf_internal.h")
+                "paper_2002_06295_gb300/csrc/mkf_geom.h")
+OVERLAP_SOURCES = ("paper_2002_06295_gb300/csrc/overlaps.cu", "paper_2002_06295_gb300/csrc/mkf_device.cuh",
+                   "paper_2002_06295_gb300/csrc/mkf_fit_common.cuh", "paper_2002_06295_gb300/csrc/mkf_geom.h")
 
 
 def kernel_digest(sources=KERNEL_SOURCES):
