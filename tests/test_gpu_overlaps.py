@@ -106,3 +106,20 @@ def test_built_tracks_recover_simulated_overlaps(event):
     assert ok / tot > 0.95, (ok, tot)
     assert fake / n_plain < 0.05, (fake, n_plain)
     ctx.close()
+
+
+def test_no_tracks_and_tracks_without_hits(event):
+    import paper_2002_06295_gb300 as mkf
+    ev = event
+    ctx, d, dev = _setup(ev)
+    z = torch.zeros((0, 38), dtype=torch.int32, device=dev)
+    o = mkf.mkf_find_overlaps(ctx, d["xyz"], d["lcov"], d["layer"], z, torch.zeros((6, 0), device=dev),
+                              torch.zeros((21, 0), device=dev))
+    assert o["hit"].numel() == 0
+    h = torch.full((3, 38), -1, dtype=torch.int32, device=dev)
+    sp = torch.tensor(ev.seed_par[:3].T.copy(), dtype=torch.float32, device=dev)
+    sc = torch.tensor(ev.seed_cov[:3].T.copy(), dtype=torch.float32, device=dev)
+    o = mkf.mkf_find_overlaps(ctx, d["xyz"], d["lcov"], d["layer"], h, sp, sc)
+    mkf.mkf_sync(ctx)
+    assert (o["hit"].cpu().numpy() == -1).all()
+    ctx.close()

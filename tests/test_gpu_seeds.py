@@ -180,3 +180,30 @@ def test_tracks_built_from_hit_seeds():
     assert len(want) > 1000
     assert n_ok / len(want) > 0.95, (n_ok, len(want))
     ctx.close()
+
+
+def test_event_without_layer0_hits_and_count_only():
+    """A batch whose middle event has no layer-0 hits: its CSR range is empty
+    and the other events match the oracle; max_seeds = 0 only counts."""
+    import oracle
+    import paper_2002_06295_gb300 as mkf
+    evs = [sev.make_config_event(2, e, n_tracks=600) for e in range(3)]
+    ids, _ = oracle.seeding_layers(evs[0].geom)
+    keep = evs[1].hit_layer != ids[0]
+    xyz = np.concatenate([evs[0].hit_xyz, evs[1].hit_xyz[keep], evs[2].hit_xyz])
+    lay = np.concatenate([evs[0].hit_layer, evs[1].hit_layer[keep], evs[2].hit_layer])
+    lcov = np.concatenate([evs[0].hit_lcov, evs[1].hit_lcov[keep], evs[2].hit_lcov])
+    off = np.cumsum([0, evs[0].n_hits, int(keep.sum()), evs[2].n_hits])
+    ctx = _ctx_for(evs[0])
+    _bin(ctx, xyz, lcov, lay, off)
+    got = mkf.mkf_seed_tracks(ctx, **CUTS)
+    mkf.mkf_sync(ctx)
+    eo = got["ev_seed_off"].cpu().numpy()
+    assert eo[2] == eo[1] and eo[1] > 0 and eo[3] > eo[2]
+    ref, loose = _oracle_pair(evs[0].geom, xyz, lay, off, CUTS)
+    _compare(got, loose, ref, off)
+    c = mkf.mkf_seed_tracks(ctx, max_seeds=0, **CUTS)
+    assert c["n"] == got["n"]
+    with pytest.raises(mkf.MkfError):
+        mkf.mkf_sync(ctx)
+    ctx.close()

@@ -120,3 +120,38 @@ def test_bad_config_rejected():
     with pytest.raises(mkf.MkfError):
         mkf.mkf_set_strip_config(ctx, 64, 4, 2)
     ctx.close()
+
+
+@pytest.mark.parametrize("n_strips,gap,bad_frac,config", [
+    (16, 1, 0.03, (32, 1, 2)),      # one ragged chunk
+    (768, 40, 0.5, (32, 1, 2)),     # half the strips bad, gaps longer than a 32-strip block
+    (768, 40, 0.5, (64, 2, 2)),
+    (512, 0, 0.5, (0, 0, 0)),
+])
+def test_extreme_gaps_and_widths(n_strips, gap, bad_frac, config):
+    import oracle
+    import paper_2002_06295_gb300 as mkf
+    rng = np.random.default_rng(90 + gap + n_strips)
+    nq, bad = strips.make_strip_calibration(400, n_strips, rng, bad_frac=bad_frac)
+    evs = [strips.make_strip_event(nq, rng, occupancy=0.05) for _ in range(2)]
+    dev = torch.device("cuda", 0)
+    ctx = mkf.Context(0)
+    mkf.mkf_set_strip_config(ctx, *config)
+    o = mkf.mkf_cluster_strips(ctx, torch.from_numpy(np.concatenate(evs, 0)).to(dev), torch.from_numpy(nq).to(dev),
+                               torch.from_numpy(bad).to(dev), max_bad_gap=gap, q_min=30)
+    n = int(o["count"].item())
+    mkf.mkf_sync(ctx)
+    _compare(o, n, _oracle(evs, nq, bad, gap, 30))
+    ctx.close()
+
+
+def test_no_events():
+    import paper_2002_06295_gb300 as mkf
+    dev = torch.device("cuda", 0)
+    ctx = mkf.Context(0)
+    nq = torch.full((10, 768), 32, dtype=torch.uint16, device=dev)
+    bad = torch.zeros((10, 768), dtype=torch.uint8, device=dev)
+    o = mkf.mkf_cluster_strips(ctx, torch.zeros((0, 768), dtype=torch.uint16, device=dev), nq, bad, max_out=16)
+    assert int(o["count"].item()) == 0
+    mkf.mkf_sync(ctx)
+    ctx.close()
