@@ -60,7 +60,8 @@ void mkf_destroy(mkf_ctx* ctx) {
                     &ctx->dd_next,  &ctx->dd_beat, &ctx->dd_nbeat,  &ctx->dd_state, &ctx->track_hits,
                     &ctx->probe_buf, &ctx->strip_bits, &ctx->seed_cnt, &ctx->seed_off, &ctx->seed_part, &ctx->seed_pairs,
                     &ctx->seed_qcnt, &ctx->seed_qoff, &ctx->grid_key, &ctx->grid_rank, &ctx->grid_cnt,
-                    &ctx->grid_off, &ctx->grid_rec, &ctx->seed_stats, &ctx->ovl_stats};
+                    &ctx->grid_off, &ctx->grid_rec, &ctx->seed_stats, &ctx->ovl_stats,
+                    &ctx->seed_scratch, &ctx->seed_loc};
   for (DevBuf* b : bufs) b->release();
   delete ctx;
 }

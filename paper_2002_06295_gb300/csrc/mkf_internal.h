@@ -87,6 +87,8 @@ struct mkf_ctx {
   mkf::DevBuf seed_cnt, seed_off, seed_part, seed_pairs, seed_qcnt, seed_qoff;   // hit-based seeding
   mkf::DevBuf grid_key, grid_rank, grid_cnt, grid_off, grid_rec;                // its search grid
   mkf::DevBuf seed_stats;                                                       // its work counters
+  mkf::DevBuf seed_scratch, seed_loc;   // per-warp triplet lists of the counting pass, their places
+  int64_t seed_trip_hint = 0;           // triplets of the last seeding call (sizes the scratch)
   mkf::DevBuf ovl_stats;                                                        // overlap-hit search counters
 
   // optional stage timing (CUDA events on the launch stream)

@@ -26,11 +26,16 @@
 // order, bins sorted by hit id) and ev_seed_off is a plain CSR:
 //  1. one warp per layer-0 hit: the rows of its layer-1 window are fetched
 //     together and the lanes test the window's hits 32 at a time; a lane whose
-//     pair passes searches that pair's layer-2 window -> triplet list;
+//     pair passes searches that pair's layer-2 window -> triplet list.  The
+//     counting pass also keeps each hit's triplets (in order) in a per-warp
+//     scratch segment, so the writing pass is a copy to the scanned places
+//     (or, if a segment overflowed, the search again);
 //  2. one thread per triplet: its layer-3 window -> seeds.
 // The triplet total is read back once (one stream synchronisation) to size
 // the triplet list; so the call returns when stage 1 is done, and it cannot be
 // captured in a CUDA graph.
+#include <algorithm>
+
 #include "mkf_device.cuh"
 #include "mkf_internal.h"
 
@@ -215,8 +220,16 @@ template <bool WRITE>
 __global__ void __launch_bounds__(kSeedThreads)
     k_seed_triplets(const SeedArgs A, const float4* __restrict__ rec, const int* __restrict__ bin_off,
                     const int* __restrict__ l0_cum, int64_t n_slots, int* __restrict__ tcnt,
-                    const int* __restrict__ toff, int4* __restrict__ trip, unsigned long long* __restrict__ stats) {
+                    const int* __restrict__ toff, int4* __restrict__ trip, unsigned long long* __restrict__ stats,
+                    int4* __restrict__ scratch, int64_t seg_cap, int64_t* __restrict__ item_loc,
+                    int* __restrict__ overflow) {
   const int lane = threadIdx.x & 31;
+  // count pass with a scratch list: the warp keeps each item's triplets, in
+  // order and contiguous, in its own segment of `scratch`
+  const bool keep = !WRITE && scratch != nullptr;
+  const int64_t seg_base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * seg_cap;
+  int64_t cursor = 0;      // used part of the warp's segment (uniform)
+  bool full = false;       // the segment overflowed (uniform)
   int st_l1 = 0, st_pairs = 0, st_l2 = 0, st_trip = 0;   // work counters (count pass; per lane)
   __shared__ int4 queue_all[kSeedThreads / 32][64];   // per warp: passing pairs in order (layer-1 position, w, g0, cot)
   int4* queue = queue_all[threadIdx.x >> 5];
@@ -277,6 +290,13 @@ __global__ void __launch_bounds__(kSeedThreads)
         for_layer2(A, ebase, q, bin_off, rec, unused,
                    [&](const SHit&, int pcpos) { trip[i++] = make_int4(pos, pb, pcpos, ebase); });
       }
+      if (keep && !full && cursor + n + group > seg_cap) full = true;
+      if (keep && !full && mine > 0) {
+        int64_t i = seg_base + cursor + n + ex;
+        int unused = 0;
+        for_layer2(A, ebase, q, bin_off, rec, unused,
+                   [&](const SHit&, int pcpos) { scratch[i++] = make_int4(pos, pb, pcpos, ebase); });
+      }
       n += group;
       queued -= cnt;
     };
@@ -315,8 +335,29 @@ __global__ void __launch_bounds__(kSeedThreads)
     while (queued > 0) drain(min(queued, 32));
     st_trip += lane == 0 ? n : 0;
     if (!WRITE && lane == 0) tcnt[item] = n;
+    if (keep) {
+      if (lane == 0) item_loc[item] = full ? -1 : seg_base + cursor;
+      if (!full) cursor += n;
+    }
   }
+  if (keep && full && lane == 0) atomicOr(overflow, 1);
   if (!WRITE) warp_add_stats(stats, st_l1, st_pairs, st_l2, st_trip, 0);
+}
+
+// The count pass's scratch lists to their places in the triplet list: one
+// warp per layer-0 hit.
+__global__ void k_seed_compact(const int* __restrict__ l0_cum, int n_events, const int* __restrict__ tcnt,
+                               const int* __restrict__ toff, const int64_t* __restrict__ item_loc,
+                               const int4* __restrict__ scratch, int4* __restrict__ trip) {
+  const int lane = threadIdx.x & 31;
+  const int n_items = __ldg(&l0_cum[n_events]);
+  const int64_t n_warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); item < n_items;
+       item += n_warps) {
+    const int cnt = __ldg(&tcnt[item]);
+    const int64_t src = __ldg(&item_loc[item]), dst = __ldg(&toff[item]);
+    for (int j = lane; j < cnt; j += 32) trip[dst + j] = __ldg(&scratch[src + j]);
+  }
 }
 
 // Stage 2: one thread per triplet, its layer-3 window.  Count pass: qcnt[j] =
@@ -568,13 +609,27 @@ extern "C" mkf_status mkf_seed_tracks(mkf_ctx* ctx, float pt_min, float z_max, f
   if ((e = cudaMemsetAsync(ctx->seed_stats.p, 0, 8 * sizeof(unsigned long long), st)) != cudaSuccess)
     return ctx->cuda_fail(e, "memset");
   unsigned long long* stats = ctx->seed_stats.as<unsigned long long>();
+  // the count pass also keeps each layer-0 hit's triplets in a per-warp
+  // scratch segment, sized from the last call's triplet total (or the hits)
+  const int64_t n_warps = (int64_t)blocks * (kSeedThreads / 32);
+  const int64_t hint = ctx->seed_trip_hint > 0 ? ctx->seed_trip_hint : H;
+  const int64_t seg_cap = std::max<int64_t>(2048, 2 * hint / n_warps + 256);
+  if ((e = ctx->seed_scratch.ensure((size_t)(n_warps * seg_cap) * sizeof(int4))) != cudaSuccess ||
+      (e = ctx->seed_loc.ensure((size_t)(H + 1) * sizeof(int64_t) + 16)) != cudaSuccess)
+    return ctx->fail(MKF_ERR_OOM, "seed scratch");
+  int* overflow = reinterpret_cast<int*>(ctx->seed_loc.as<char>() + (size_t)(H + 1) * sizeof(int64_t));
+  if ((e = cudaMemsetAsync(overflow, 0, sizeof(int), st)) != cudaSuccess) return ctx->cuda_fail(e, "memset");
   if (H > 0)
-    k_seed_triplets<false><<<blocks, kSeedThreads, 0, st>>>(A, rec, bin_off, l0_cum, H, pcnt, nullptr, nullptr, stats);
+    k_seed_triplets<false><<<blocks, kSeedThreads, 0, st>>>(A, rec, bin_off, l0_cum, H, pcnt, nullptr, nullptr, stats,
+                                                             ctx->seed_scratch.as<int4>(), seg_cap,
+                                                             ctx->seed_loc.as<int64_t>(), overflow);
   if ((e = launch_excl_scan(pcnt, H, poff, ctx->seed_part, st)) != cudaSuccess) return ctx->cuda_fail(e, "triplet scan");
-  int n_trip = 0;
+  int n_trip = 0, over = 0;
   if ((e = cudaMemcpyAsync(&n_trip, poff + H, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(&over, overflow, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
       (e = cudaStreamSynchronize(st)) != cudaSuccess)
     return ctx->cuda_fail(e, "triplet count");
+  ctx->seed_trip_hint = n_trip;
   const int64_t P = n_trip;
   if ((e = ctx->seed_pairs.ensure((size_t)(P + 1) * sizeof(int4))) != cudaSuccess ||
       (e = ctx->seed_qcnt.ensure((size_t)(P + 1) * 4)) != cudaSuccess ||
@@ -583,8 +638,12 @@ extern "C" mkf_status mkf_seed_tracks(mkf_ctx* ctx, float pt_min, float z_max, f
   int4* trip = ctx->seed_pairs.as<int4>();
   int* qcnt = ctx->seed_qcnt.as<int>();
   int* qoff = ctx->seed_qoff.as<int>();
-  if (H > 0)
-    k_seed_triplets<true><<<blocks, kSeedThreads, 0, st>>>(A, rec, bin_off, l0_cum, H, nullptr, poff, trip, stats);
+  if (H > 0 && !over)   // scratch lists in place: move them
+    k_seed_compact<<<blocks, kSeedThreads, 0, st>>>(l0_cum, E, pcnt, poff, ctx->seed_loc.as<int64_t>(),
+                                                    ctx->seed_scratch.as<int4>(), trip);
+  else if (H > 0)        // a segment overflowed: search again and write
+    k_seed_triplets<true><<<blocks, kSeedThreads, 0, st>>>(A, rec, bin_off, l0_cum, H, nullptr, poff, trip, stats,
+                                                            nullptr, 0, nullptr, nullptr);
   // stage 2 over the triplet list
   if (P > 0)
     k_seed_quads<false><<<blocks, kSeedThreads, 0, st>>>(A, rec, bin_off, trip, (int)P, qcnt, nullptr, nullptr,
