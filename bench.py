@@ -207,7 +207,7 @@ def measure_batched(mkf, tune, dev, reps=3):
     import synth
     b = synth.make_batch(3)
     g = b.geom
-    spec = synth.CONFIGS[3]
+    spec = synth.WORKLOAD_SPECS[3]
     kw = dict(chi2_cut=spec["chi2_cut"], max_cands=spec["max_cands"], max_holes=spec["max_holes"],
               min_hits=spec["min_hits"], dup_frac=spec["dup_frac"])
     f32 = dict(dtype=torch.float32, device=dev)
@@ -638,11 +638,11 @@ def main():
     if cfg_id == 2:
         evs = [synth.make_config_event(2, rank)]
     else:
-        evs = [synth.make_config_event(cfg_id, rank * 10000 + e) for e in range(synth.CONFIGS[cfg_id]["n_events"])]
+        evs = [synth.make_config_event(cfg_id, rank * 10000 + e) for e in range(synth.WORKLOAD_SPECS[cfg_id]["n_events"])]
     g = evs[0].geom
     ctx = mkf.Context(local)
     mkf.mkf_load_geometry(ctx, g.table(), g.bz, 64, 16)
-    spec = synth.CONFIGS[cfg_id]
+    spec = synth.WORKLOAD_SPECS[cfg_id]
     f32 = dict(dtype=torch.float32)
     cat = lambda name: np.concatenate([getattr(e, name) for e in evs], 0)
     n_hits = int(sum(e.n_hits for e in evs))

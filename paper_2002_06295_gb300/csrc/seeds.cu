@@ -484,14 +484,11 @@ __global__ void k_grid_order(const int* __restrict__ goff, int64_t n_cells, floa
   }
 }
 
-// layer-0 hits of each event: n0[e] = positions of its layer-0 bins
-// and ev_pos0[e] = first binned position of event e (e = 0..E)
+// layer-0 hits of each event: n0[e] = positions of its layer-0 cells
 __global__ void k_seed_l0_counts(const int* __restrict__ bin_off, int64_t bins_per_event, int base0, int nb0,
-                                 int n_events, int* __restrict__ n0, int* __restrict__ ev_pos0) {
+                                 int n_events, int* __restrict__ n0) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e > n_events) return;
-  ev_pos0[e] = bin_off[(int64_t)e * bins_per_event];
-  if (e == n_events) return;
+  if (e >= n_events) return;
   const int64_t b = (int64_t)e * bins_per_event + base0;
   n0[e] = bin_off[b + nb0] - bin_off[b];
 }
@@ -559,7 +556,7 @@ extern "C" mkf_status mkf_seed_tracks(mkf_ctx* ctx, float pt_min, float z_max, f
   const int64_t H = ctx->n_hits;
   const int E = ctx->n_events;
   cudaError_t e;
-  // seed_cnt: pcnt [H] | n0 [E + 1]; seed_off: poff [H + 1] | l0_cum [E + 1] | ev_pos0 [E + 1];
+  // seed_cnt: pcnt [H] | n0 [E + 1]; seed_off: poff [H + 1] | l0_cum [E + 1];
   // seed_pairs, seed_qcnt, seed_qoff: pair list, its seed counts and their scan; seed_part: scan scratch
   if ((e = ctx->seed_cnt.ensure((size_t)(H + E + 2) * 4)) != cudaSuccess) return ctx->fail(MKF_ERR_OOM, "seed counts");
   if ((e = ctx->seed_off.ensure((size_t)(H + 2 * E + 4) * 4)) != cudaSuccess)
@@ -596,9 +593,9 @@ extern "C" mkf_status mkf_seed_tracks(mkf_ctx* ctx, float pt_min, float z_max, f
   int* n0 = pcnt + H;
   int* poff = ctx->seed_off.as<int>();
   int* l0_cum = poff + H + 1;
-  int* ev_pos0 = l0_cum + E + 1;
-  k_seed_l0_counts<<<(unsigned)((E + 1 + T - 1) / T), T, 0, st>>>(ctx->grid_off.as<int>(), A.bins_per_event,
-                                                                   A.L[0].bin_base, kGridCells, E, n0, ev_pos0);
+  if (E > 0)
+    k_seed_l0_counts<<<(unsigned)((E + T - 1) / T), T, 0, st>>>(ctx->grid_off.as<int>(), A.bins_per_event,
+                                                                 A.L[0].bin_base, kGridCells, E, n0);
   if ((e = launch_excl_scan(n0, E, l0_cum, ctx->seed_part, st)) != cudaSuccess) return ctx->cuda_fail(e, "scan");
   if (H > 0 && (e = cudaMemsetAsync(pcnt, 0, (size_t)H * 4, st)) != cudaSuccess) return ctx->cuda_fail(e, "memset");
   const unsigned blocks = (unsigned)(ctx->n_sm * 8);   // persistent: 32 warps per SM

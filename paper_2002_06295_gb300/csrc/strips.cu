@@ -62,9 +62,9 @@ __device__ __forceinline__ void put_cluster(const Cluster& c, unsigned long long
 
 // Cluster being grown along one row (plain kernel).  d = sum (64 a^2 -
 // 25 nq^2), so the quadrature test is d > 0; qi = sum (i - first) a, the first
-// moment about the first strip.
+// moment about the first strip; pend = bad strips since the last candidate.
 struct Run {
-  int first, last, prev, pend;
+  int first, last, pend;
   bool open, seeded;
   long long q, d, qi;
 };
@@ -477,7 +477,7 @@ __global__ void __launch_bounds__(kFallbackThreads)
   const uint16_t* a_row = adc + row * n_strips;
   const uint16_t* n_row = noise_q + m * n_strips;
   const uint8_t* b_row = bad + m * n_strips;
-  Run s{0, 0, -2, 0, false, false, 0, 0, 0};
+  Run s{0, 0, 0, false, false, 0, 0, 0};
   auto close = [&]() {
     if (run_kept(s, q_min))
       put_cluster(run_cluster(s, (int)row), atomicAdd(count, 1ull), out_row, out_first, out_last, out_charge,
@@ -595,7 +595,7 @@ cudaError_t launch_tma(mkf_ctx* ctx, const uint16_t* adc, const uint16_t* noise_
 
 namespace {
 // Work splits the TMA kernel is built for: strips per chunk, events per item, stages.
-constexpr int kStripConfigs[][3] = {{32, 1, 2}, {32, 1, 3}, {32, 1, 4}, {32, 2, 2},
+constexpr int kStripSplits[][3] = {{32, 1, 2}, {32, 1, 3}, {32, 1, 4}, {32, 2, 2},
                                     {64, 1, 2}, {64, 1, 3}, {64, 2, 2}};
 constexpr int kStripDefault[3] = {32, 1, 2};
 }  // namespace
@@ -603,7 +603,7 @@ constexpr int kStripDefault[3] = {32, 1, 2};
 extern "C" mkf_status mkf_set_strip_config(mkf_ctx* ctx, int chunk, int events_per_item, int stages) {
   if (!ctx) return MKF_ERR_ARG;
   bool ok = chunk == 0 && events_per_item == 0 && stages == 0;
-  for (const auto& k : kStripConfigs) ok |= k[0] == chunk && k[1] == events_per_item && k[2] == stages;
+  for (const auto& k : kStripSplits) ok |= k[0] == chunk && k[1] == events_per_item && k[2] == stages;
   if (!ok) return ctx->fail(MKF_ERR_ARG, "strip config: not one of the built work splits");
   ctx->strip_chunk = chunk;
   ctx->strip_events = events_per_item;

@@ -9,8 +9,8 @@ imports the other.
 """
 from .geometry import Geometry, geometry_barrel10, geometry_barrel14, geometry_cmslike
 from .events import (Event, EventBatch, simulate_event, make_config_event, make_batch,
-                     CONFIGS, config_seed)
+                     WORKLOAD_SPECS, config_seed)
 
 __all__ = ["Geometry", "geometry_barrel10", "geometry_barrel14", "geometry_cmslike",
            "Event", "EventBatch", "simulate_event", "make_config_event", "make_batch",
-           "CONFIGS", "config_seed"]
+           "WORKLOAD_SPECS", "config_seed"]

@@ -310,7 +310,7 @@ def simulate_event(geom: Geometry, n_tracks: int, rng: np.random.Generator, *,
 # ---------------------------------------------------------------------------
 # The five workloads (C1..C5).  Each entry: geometry factory, track count(s),
 # kinematic ranges, noise fraction and the reconstruction limits.
-CONFIGS = {
+WORKLOAD_SPECS = {
     1: dict(name="C1 plain build, barrel10, 100 tracks", geom=geometry_barrel10, n_events=1,
             tracks=100, pt_range=(0.5, 10.0), pt_log=False, eta_max=1.0, noise_frac=0.0,
             chi2_cut=30.0, max_cands=4, max_holes=3, min_hits=4, dup_frac=0.5),
@@ -339,7 +339,7 @@ def _n_tracks(spec, rng):
 
 
 def make_config_event(config: int, event: int = 0, n_tracks=None, overlap_frac=0.0) -> Event:
-    spec = CONFIGS[config]
+    spec = WORKLOAD_SPECS[config]
     rng = np.random.default_rng(config_seed(config, event))
     n = _n_tracks(spec, rng) if n_tracks is None else int(n_tracks)
     return simulate_event(spec["geom"](), n, rng, pt_range=spec["pt_range"], pt_log=spec["pt_log"],
@@ -347,7 +347,7 @@ def make_config_event(config: int, event: int = 0, n_tracks=None, overlap_frac=0
 
 
 def make_batch(config: int, n_events=None, n_tracks=None) -> EventBatch:
-    spec = CONFIGS[config]
+    spec = WORKLOAD_SPECS[config]
     E = spec["n_events"] if n_events is None else int(n_events)
     evs = [make_config_event(config, e, n_tracks) for e in range(E)]
     hoff = np.zeros(E + 1, np.int64)

@@ -111,7 +111,7 @@ def test_capacity_is_reported():
 
 def test_splits_match_binding():
     import paper_2002_06295_gb300.api as api
-    assert tuple(api.STRIP_CONFIGS) == _SPLITS
+    assert tuple(api.STRIP_SPLITS) == _SPLITS
 
 
 def test_bad_config_rejected():
