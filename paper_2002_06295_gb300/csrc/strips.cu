@@ -636,8 +636,12 @@ extern "C" mkf_status mkf_cluster_strips(mkf_ctx* ctx, const uint16_t* adc, cons
                    (uintptr_t)bad % 16 == 0;
   if (tma) {
     bool encoded = false;
+    // default: one event per item for small batches (more, shorter items fill
+    // the GPU evenly); two from 32 events up (the calibration is staged once
+    // for both, and there are items enough)
     const bool dflt = ctx->strip_chunk == 0;
-    const int ch = dflt ? kStripDefault[0] : ctx->strip_chunk, ev = dflt ? kStripDefault[1] : ctx->strip_events,
+    const int ch = dflt ? kStripDefault[0] : ctx->strip_chunk,
+              ev = dflt ? (n_events >= 32 ? 2 : kStripDefault[1]) : ctx->strip_events,
               ns = dflt ? kStripDefault[2] : ctx->strip_stages;
 #define MKF_STRIP_ARGS                                                                                           \
   ctx, adc, noise_q, bad, n_events, n_modules, n_strips, max_bad_gap, q_min, out_row, out_first, out_last, \

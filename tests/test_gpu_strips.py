@@ -145,6 +145,15 @@ def test_extreme_gaps_and_widths(n_strips, gap, bad_frac, config):
     ctx.close()
 
 
+def test_default_split_for_many_events():
+    """From 32 events up the default takes two events per item."""
+    import paper_2002_06295_gb300 as mkf
+    ctx, o, n, ref = _run(200, 768, 40, 1, seed=77)
+    mkf.mkf_sync(ctx)
+    _compare(o, n, ref)
+    ctx.close()
+
+
 def test_no_events():
     import paper_2002_06295_gb300 as mkf
     dev = torch.device("cuda", 0)
