@@ -83,6 +83,14 @@ __device__ __forceinline__ float prop_pass(int e, const float p0[6], const FitHi
   return acc_e;
 }
 
+// The listed slot before slot k of a track's hit row (-1 when there is none).
+__device__ __forceinline__ int prev_listed(const int* __restrict__ row, int k) {
+  do {
+    --k;
+  } while (k >= 0 && row[k] < 0);
+  return k;
+}
+
 template <int LPT>
 __global__ void __launch_bounds__(kAdjThreads)
     k_fit_adjoint(const GeomDev* __restrict__ g, const float* __restrict__ xyz, const float* __restrict__ lcov,
@@ -112,7 +120,10 @@ __global__ void __launch_bounds__(kAdjThreads)
       }
     const float chib = g_chi2 ? g_chi2[t] : 0.0f;
     const int* row = hits + t * K;
-    for (int k = K - 1; k >= 0; --k) {
+    // The group walks its track's listed hits only (prev_listed skips the
+    // empty slots), so a warp runs the body once per hit of its longest track
+    // rather than once per slot.
+    for (int k = prev_listed(row, K); k >= 0; k = prev_listed(row, k)) {
       const int h = row[k];
       FitHit<float> f;
       if (!load_fit_hit(g, xyz, lcov, layer, H, h, align, x0, f)) continue;
