@@ -410,7 +410,7 @@ __device__ __forceinline__ bool step_inward(const InwardHit& f, double p[6], f2 
 // double-float and the residuals and the state in FP64.  The measurement rows
 // are rounded to FP32 for the covariance (a frame turned by ~1e-8 rad, used
 // consistently there); the residuals use the FP64 rows.  The state increment
-// K r is formed in FP64 from the double-float gain: in the early, weakly
+// K r is formed in double-float and then added in FP64: in the early, weakly
 // constrained updates its terms are large and nearly cancel, and an FP32
 // increment put the curvature of short-lever-arm tracks 2e-4 off.  The chi2
 // needs no more than FP32.  Returns the predicted chi2.
@@ -455,7 +455,8 @@ __device__ __forceinline__ double update_inward(const InwardHit& f, double p[6],
   // residuals in FP64
   const double ra = fma(m.s, p[0], -m.c * p[1]);
   const double rb = kind == 0 ? m.w - p[2] : m.w - fma(m.c, p[0], m.s * p[1]);
-  const float raf = float(ra), rbf = float(rb);
+  const f2 ra2 = f2_of(ra), rb2 = f2_of(rb);
+  const float raf = ra2.h, rbf = rb2.h;
   const float chi2 = fmaf(Waa.h * raf, raf, fmaf(2.0f * Wab.h * raf, rbf, Wbb.h * rbf * rbf));
   f2 Kg[6][2];
 #pragma unroll
@@ -468,8 +469,12 @@ __device__ __forceinline__ double update_inward(const InwardHit& f, double p[6],
     Kg[i][0] = f2acc_get(k0);
     Kg[i][1] = f2acc_get(k1);
     // the two terms can be large and nearly cancel (early, weakly constrained
-    // updates): the increment is formed in FP64
-    p[i] = fma(double(Kg[i][0].h) + double(Kg[i][0].l), ra, fma(double(Kg[i][1].h) + double(Kg[i][1].l), rb, p[i]));
+    // updates): the increment is formed in double-float, then widened
+    f2acc dp{0.0f, 0.0f};
+    f2acc_add_mul(dp, Kg[i][0], ra2);
+    f2acc_add_mul(dp, Kg[i][1], rb2);
+    const f2 d = f2acc_get(dp);
+    p[i] += double(d.h) + double(d.l);
   }
   p[4] = wrap_phi(p[4]);
 #pragma unroll
