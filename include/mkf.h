@@ -359,11 +359,10 @@ mkf_status mkf_fit_tracks(mkf_ctx* ctx, const float* xyz, const float* lcov, con
  * with the outermost hit in place, then propagates inward (negative path) to
  * each earlier hit, adds its material and updates.  Arguments as
  * mkf_fit_tracks (init_cov is ignored; ckpt unsupported, pass NULL).
- * Arithmetic: state, transport, residuals and state increments in FP64; the
- * covariance algebra (transport J C J^T, gain, C - K B^T) in double-float
- * (pairs of floats, ~48 significant bits); the multiple-scattering term and
- * the chi2 in FP32; outputs rounded to FP32.  (The prior makes the first
- * updates shrink variances by up to 1e5, which FP32 cannot carry.) */
+ * Arithmetic: FP64 (the multiple-scattering term in FP32); outputs rounded
+ * to FP32.  The prior makes the first updates shrink variances by up to 1e5,
+ * and mixed barrel/disk tracks keep correlations close to 1, which neither
+ * FP32 nor a 48-bit float pair carries to 1e-4 on every track. */
 mkf_status mkf_fit_backward(mkf_ctx* ctx, const float* xyz, const float* lcov, const int* layer, int64_t n_hits,
                             const int* hits, int K, const float* init_par, int64_t n_tracks, const float* align,
                             const float* x0, float* out_par, float* out_cov, float* out_chi2, int* out_ok,

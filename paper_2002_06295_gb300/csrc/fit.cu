@@ -80,14 +80,13 @@ __device__ __forceinline__ int prev_listed(const int* __restrict__ row, int k) {
 //    Jacobian and the material term; 1/(q A) for both roots of the crossing
 //    quadratic);
 //  * atan(t)/t comes from its Taylor series for |t| < 0.1 (the usual step);
-//  * the covariance algebra runs in double-float on the FP32 pipes (below).
+//  * J C J^T uses the rank-one form of the Jacobian (similarity_rank1).
 
 struct InwardHit {
   int kind;
   double pos;     // surface r (barrel) or z (disk), aligned
   float x0;       // thickness
   Meas<double> m;
-  float v00, v01, v11;   // the hit's covariance as stored (FP32)
 };
 
 // load_fit_hit in FP64 with the hit's unit vector from one rsqrt.
@@ -116,12 +115,9 @@ __device__ __forceinline__ bool load_inward_hit(const GeomDev* __restrict__ g, c
   f.m.c = (x * cd - y * sd) * ir;
   f.m.s = (x * sd + y * cd) * ir;
   f.m.w = ly.kind == 0 ? z + dz : r2 * ir + dr;
-  f.v00 = lcov[h];
-  f.v11 = lcov[H + h];
-  f.v01 = lcov[2 * H + h];
-  f.m.v00 = double(f.v00);
-  f.m.v11 = double(f.v11);
-  f.m.v01 = double(f.v01);
+  f.m.v00 = double(lcov[h]);
+  f.m.v11 = double(lcov[H + h]);
+  f.m.v01 = double(lcov[2 * H + h]);
   return true;
 }
 
@@ -175,166 +171,47 @@ __device__ __forceinline__ double cylinder_path_inward(double x0, double y0, dou
   return s;
 }
 
-// ---- double-float arithmetic for the inward fit's covariance
-//
-// A value is held as the unevaluated sum h + l of two floats (about 48
-// significant bits), built from error-free transformations: TwoSum (Knuth),
-// FastTwoSum (Dekker) and the exact product error fma(a, b, -a b).  The
-// __f*_rn intrinsics keep the compiler from contracting their adds and
-// multiplies into FMAs, which would break the transformations.  The
-// covariance needs far more than FP32 (the first updates shrink variances by
-// up to 1e5, and mixed barrel/disk tracks keep correlations close to 1) but far
-// less than FP64's 53 bits, and the FP32 pipes are idle in this kernel while
-// its FP64 unit is the bottleneck.
-struct f2 {
-  float h, l;
-};
-
-__device__ __forceinline__ f2 f2_fast_two_sum(float a, float b) {   // needs |a| >= |b| (or a = 0)
-  const float s = __fadd_rn(a, b);
-  return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ f2 f2_two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
-}
-__device__ __forceinline__ f2 f2_of(double x) {
-  const float h = float(x);
-  return {h, float(x - double(h))};
-}
-__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
-  const f2 s = f2_two_sum(a.h, b.h);
-  return f2_fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
-}
-__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
-  const float p = __fmul_rn(a.h, b.h);
-  return f2_fast_two_sum(p, fmaf(a.h, b.l, fmaf(a.l, b.h, fmaf(a.h, b.h, -p))));
-}
-__device__ __forceinline__ f2 f2_mulf(f2 a, float b) {
-  const float p = __fmul_rn(a.h, b);
-  return f2_fast_two_sum(p, fmaf(a.l, b, fmaf(a.h, b, -p)));
-}
-// 1/d: the float reciprocal refined by one Newton step, e = 1 - d y exactly to
-// double-float precision (1 - (d y)_h is exact near 1).
-__device__ __forceinline__ f2 f2_recip(f2 d) {
-  const float y = __frcp_rn(d.h);
-  const f2 t = f2_mulf(d, y);
-  const float e = __fsub_rn(__fsub_rn(1.0f, t.h), t.l);
-  return f2_fast_two_sum(y, __fmul_rn(y, e));
-}
-
-// A running sum of products: s collects the leading parts by TwoSum, c the
-// rounding errors and low-order terms (float), normalised once at the end.
-struct f2acc {
-  float s, c;
-};
-__device__ __forceinline__ f2acc f2acc_of(f2 x) { return {x.h, x.l}; }
-__device__ __forceinline__ void f2acc_add_mulf(f2acc& a, f2 x, float y) {   // a += x y
-  const float p = __fmul_rn(x.h, y);
-  const float e = fmaf(x.l, y, fmaf(x.h, y, -p));
-  const f2 t = f2_two_sum(a.s, p);
-  a.s = t.h;
-  a.c = __fadd_rn(a.c, __fadd_rn(t.l, e));
-}
-__device__ __forceinline__ void f2acc_add_mul(f2acc& a, f2 x, f2 y) {   // a += x y
-  const float p = __fmul_rn(x.h, y.h);
-  const float e = fmaf(x.h, y.l, fmaf(x.l, y.h, fmaf(x.h, y.h, -p)));
-  const f2 t = f2_two_sum(a.s, p);
-  a.s = t.h;
-  a.c = __fadd_rn(a.c, __fadd_rn(t.l, e));
-}
-__device__ __forceinline__ f2 f2acc_get(const f2acc& a) { return f2_two_sum(a.s, a.c); }
-
 // C <- J C J^T for J = A + v w^T on the rows (x, y, z, phi), kappa and theta
-// rows the identity, C in double-float and J's factors in FP32 (a Jacobian
-// off by ~1e-7 relative transports C by a slightly different map, which keeps
-// it a covariance; the rounding of C itself is what needs the precision).
-// With u = C w: J C = A C + v u^T and J C J^T = (J C) A^T + z v^T with
-// z = J C w = A u + (w.u) v; A's fixed ones and zeros leave 139 products
-// instead of the dense 204.
-__device__ __forceinline__ void similarity_rank1_f2(float a03, float a04, float a13, float a14, float a25, float a33,
-                                                    const float v[4], const float w[6], f2 C[21]) {
-  f2 u[6];
+// rows the identity.  With u = C w: J C = A C + v u^T and
+// J C J^T = (J C) A^T + z v^T with z = J C w = A u + (w.u) v.  A's fixed ones
+// and zeros (transport_jacobian) leave 139 FMAs instead of the dense 204.
+__device__ __forceinline__ void similarity_rank1(double a03, double a04, double a13, double a14, double a25,
+                                                 double a33, const double v[4], const double w[6], double C[21]) {
+  double u[6];
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
-    f2acc acc{0.0f, 0.0f};
+    double acc = C[ci(k, 0)] * w[0];
 #pragma unroll
-    for (int j = 0; j < 6; ++j) f2acc_add_mulf(acc, C[ci(k, j)], w[j]);
-    u[k] = f2acc_get(acc);
+    for (int j = 1; j < 6; ++j) acc = fma(C[ci(k, j)], w[j], acc);
+    u[k] = acc;
   }
-  f2 JC[4][6];
+  double JC[4][6];
 #pragma unroll
   for (int j = 0; j < 6; ++j) {
-    f2acc r0 = f2acc_of(C[ci(0, j)]);
-    f2acc_add_mulf(r0, C[ci(3, j)], a03);
-    f2acc_add_mulf(r0, C[ci(4, j)], a04);
-    f2acc_add_mulf(r0, u[j], v[0]);
-    JC[0][j] = f2acc_get(r0);
-    f2acc r1 = f2acc_of(C[ci(1, j)]);
-    f2acc_add_mulf(r1, C[ci(3, j)], a13);
-    f2acc_add_mulf(r1, C[ci(4, j)], a14);
-    f2acc_add_mulf(r1, u[j], v[1]);
-    JC[1][j] = f2acc_get(r1);
-    f2acc r2 = f2acc_of(C[ci(2, j)]);
-    f2acc_add_mulf(r2, C[ci(5, j)], a25);
-    f2acc_add_mulf(r2, u[j], v[2]);
-    JC[2][j] = f2acc_get(r2);
-    f2acc r3 = f2acc_of(C[ci(4, j)]);
-    f2acc_add_mulf(r3, C[ci(3, j)], a33);
-    f2acc_add_mulf(r3, u[j], v[3]);
-    JC[3][j] = f2acc_get(r3);
+    JC[0][j] = fma(v[0], u[j], fma(a04, C[ci(4, j)], fma(a03, C[ci(3, j)], C[ci(0, j)])));
+    JC[1][j] = fma(v[1], u[j], fma(a14, C[ci(4, j)], fma(a13, C[ci(3, j)], C[ci(1, j)])));
+    JC[2][j] = fma(v[2], u[j], fma(a25, C[ci(5, j)], C[ci(2, j)]));
+    JC[3][j] = fma(v[3], u[j], fma(a33, C[ci(3, j)], C[ci(4, j)]));
   }
-  f2acc wa{0.0f, 0.0f};
+  double wu = u[0] * w[0];
 #pragma unroll
-  for (int j = 0; j < 6; ++j) f2acc_add_mulf(wa, u[j], w[j]);
-  const f2 wu = f2acc_get(wa);
-  f2 zz[4];
-  {
-    f2acc z0 = f2acc_of(u[0]);
-    f2acc_add_mulf(z0, u[3], a03);
-    f2acc_add_mulf(z0, u[4], a04);
-    f2acc_add_mulf(z0, wu, v[0]);
-    zz[0] = f2acc_get(z0);
-    f2acc z1 = f2acc_of(u[1]);
-    f2acc_add_mulf(z1, u[3], a13);
-    f2acc_add_mulf(z1, u[4], a14);
-    f2acc_add_mulf(z1, wu, v[1]);
-    zz[1] = f2acc_get(z1);
-    f2acc z2 = f2acc_of(u[2]);
-    f2acc_add_mulf(z2, u[5], a25);
-    f2acc_add_mulf(z2, wu, v[2]);
-    zz[2] = f2acc_get(z2);
-    f2acc z3 = f2acc_of(u[4]);
-    f2acc_add_mulf(z3, u[3], a33);
-    f2acc_add_mulf(z3, wu, v[3]);
-    zz[3] = f2acc_get(z3);
-  }
+  for (int j = 1; j < 6; ++j) wu = fma(u[j], w[j], wu);
+  double zz[4];
+  zz[0] = fma(wu, v[0], fma(a04, u[4], fma(a03, u[3], u[0])));
+  zz[1] = fma(wu, v[1], fma(a14, u[4], fma(a13, u[3], u[1])));
+  zz[2] = fma(wu, v[2], fma(a25, u[5], u[2]));
+  zz[3] = fma(wu, v[3], fma(a33, u[3], u[4]));
   constexpr int R[4] = {0, 1, 2, 4};
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    // (J C A^T)[i][l] + z_i v_l for the rows l <= i
+    // (J C A^T)[i][l] for the rows l <= i, plus z_i v_l
+    const double o0 = fma(zz[i], v[0], fma(a04, JC[i][4], fma(a03, JC[i][3], JC[i][0])));
+    const double o1 = fma(zz[i], v[1], fma(a14, JC[i][4], fma(a13, JC[i][3], JC[i][1])));
+    const double o2 = fma(zz[i], v[2], fma(a25, JC[i][5], JC[i][2]));
+    const double o3 = fma(zz[i], v[3], fma(a33, JC[i][3], JC[i][4]));
+    const double o[4] = {o0, o1, o2, o3};
 #pragma unroll
-    for (int l = 0; l <= i; ++l) {
-      f2acc o;
-      if (l == 0) {
-        o = f2acc_of(JC[i][0]);
-        f2acc_add_mulf(o, JC[i][3], a03);
-        f2acc_add_mulf(o, JC[i][4], a04);
-      } else if (l == 1) {
-        o = f2acc_of(JC[i][1]);
-        f2acc_add_mulf(o, JC[i][3], a13);
-        f2acc_add_mulf(o, JC[i][4], a14);
-      } else if (l == 2) {
-        o = f2acc_of(JC[i][2]);
-        f2acc_add_mulf(o, JC[i][5], a25);
-      } else {
-        o = f2acc_of(JC[i][4]);
-        f2acc_add_mulf(o, JC[i][3], a33);
-      }
-      f2acc_add_mulf(o, zz[i], v[l]);
-      C[ci(R[i], R[l])] = f2acc_get(o);
-    }
+    for (int l = 0; l <= i; ++l) C[ci(R[i], R[l])] = o[l];
   }
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
@@ -348,48 +225,42 @@ struct InwardTrig {
   double cph, sph, cth, sth;
 };
 
-// step_to (dir < 0) with the state and path in FP64, the Jacobian's factors in
-// FP32 from the FP64 crossing, and C in double-float; updates tr to the
+// step_to (dir < 0) in FP64 with the cached trigonometry; updates tr to the
 // crossing.  Returns false when the surface is not reached.
-__device__ __forceinline__ bool step_inward(const InwardHit& f, double p[6], f2 C[21], double ck, InwardTrig& tr) {
+__device__ __forceinline__ bool step_inward(const InwardHit& f, double p[6], double C[21], double ck, InwardTrig& tr) {
   const double rs = 1.0 / tr.sth;
-  const double cot_t = tr.cth * rs;
+  const double cot_t = tr.cth * rs, inv_s2 = rs * rs;
   const double omega = ck * p[3];
-  double s;
+  double s, ict = 0.0;
   if (f.kind == 0) {
     s = cylinder_path_inward(p[0], p[1], tr.cph, tr.sph, omega, f.pos);
   } else {
-    s = (f.pos - p[2]) / cot_t;
+    ict = 1.0 / cot_t;
+    s = (f.pos - p[2]) * ict;
     if (!(s < 0.0)) s = -INFINITY;
   }
   if (!(fabs(s) < INFINITY)) return false;
   const HelixPt<double> h = helix_at(p[0], p[1], p[2], p[4], tr.cph, tr.sph, cot_t, omega, s);
-  // Jacobian factors (transport_jacobian) in FP32: A's free entries, v = dp/ds,
-  // w = ds*/dp0; displacements are formed in FP64 before rounding
-  const float fck = float(ck), fs = float(s), rsf = float(rs);
-  const float inv_s2f = rsf * rsf;
-  const float hx = float(h.x), hy = float(h.y), cph = float(h.cphi), sph = float(h.sphi);
-  const float cotf = float(cot_t), omf = float(omega);
-  const float a03 = fck * float(h.dx_dom), a04 = -float(h.y - p[1]);
-  const float a13 = fck * float(h.dy_dom), a14 = float(h.x - p[0]);
-  const float a25 = -fs * inv_s2f, a33 = fck * fs;
-  const float v[4] = {cph, sph, cotf, omf};
-  float w[6];
+  // Jacobian factors (transport_jacobian): A's free entries, v = dp/ds, w = ds*/dp0
+  const double a03 = ck * h.dx_dom, a04 = -(h.y - p[1]);
+  const double a13 = ck * h.dy_dom, a14 = h.x - p[0];
+  const double a25 = -s * inv_s2, a33 = ck * s;
+  const double v[4] = {h.cphi, h.sphi, cot_t, omega};
+  double w[6];
   if (f.kind == 0) {
-    const float inv_ds = -1.0f / fmaf(hx, cph, hy * sph);
-    w[0] = inv_ds * hx;
-    w[1] = inv_ds * hy;
-    w[2] = 0.0f;
-    w[3] = inv_ds * fmaf(hx, a03, hy * a13);
-    w[4] = inv_ds * fmaf(hx, a04, hy * a14);
-    w[5] = 0.0f;
+    const double inv_ds = -1.0 / fma(h.x, h.cphi, h.y * h.sphi);
+    w[0] = inv_ds * h.x;
+    w[1] = inv_ds * h.y;
+    w[2] = 0.0;
+    w[3] = inv_ds * fma(h.x, a03, h.y * a13);
+    w[4] = inv_ds * fma(h.x, a04, h.y * a14);
+    w[5] = 0.0;
   } else {
-    const float inv_ct = -1.0f / cotf;
-    w[0] = w[1] = w[3] = w[4] = 0.0f;
-    w[2] = inv_ct;
-    w[5] = inv_ct * a25;
+    w[0] = w[1] = w[3] = w[4] = 0.0;
+    w[2] = -ict;
+    w[5] = -ict * a25;
   }
-  similarity_rank1_f2(a03, a04, a13, a14, a25, a33, v, w, C);
+  similarity_rank1(a03, a04, a13, a14, a25, a33, v, w, C);
   p[0] = h.x;
   p[1] = h.y;
   p[2] = h.z;
@@ -397,101 +268,17 @@ __device__ __forceinline__ bool step_inward(const InwardHit& f, double p[6], f2 
   tr.cph = h.cphi;
   tr.sph = h.sphi;
   if (f.x0 > 0.0f) {
-    const float th2 = highland_theta0_sq(f.kind, f.x0, hx, hy, cph, sph, float(p[3]), float(tr.sth),
-                                         float(tr.cth));
-    const float pr = __fmul_rn(th2, inv_s2f);
-    C[ci(4, 4)] = f2_add(C[ci(4, 4)], f2{pr, fmaf(th2, inv_s2f, -pr)});
-    C[ci(5, 5)] = f2_add(C[ci(5, 5)], f2{th2, 0.0f});
+    const float th2 = highland_theta0_sq(f.kind, f.x0, float(h.x), float(h.y), float(h.cphi), float(h.sphi),
+                                         float(p[3]), float(tr.sth), float(tr.cth));
+    C[ci(4, 4)] = fma(double(th2), inv_s2, C[ci(4, 4)]);
+    C[ci(5, 5)] += double(th2);
   }
   return true;
 }
 
-// kf_update (plain form C - K B^T) with the covariance algebra in
-// double-float and the residuals and the state in FP64.  The measurement rows
-// are rounded to FP32 for the covariance (a frame turned by ~1e-8 rad, used
-// consistently there); the residuals use the FP64 rows.  The state increment
-// K r is formed in double-float and then added in FP64: in the early, weakly
-// constrained updates its terms are large and nearly cancel, and an FP32
-// increment put the curvature of short-lever-arm tracks 2e-4 off.  The chi2
-// needs no more than FP32.  Returns the predicted chi2.
-__device__ __forceinline__ double update_inward(const InwardHit& f, double p[6], f2 C[21]) {
-  const int kind = f.kind;
-  const Meas<double>& m = f.m;
-  const float c = float(m.c), sn = float(m.s);
-  f2 B[6][2];
-#pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    f2acc b0{0.0f, 0.0f};
-    f2acc_add_mulf(b0, C[ci(i, 0)], -sn);
-    f2acc_add_mulf(b0, C[ci(i, 1)], c);
-    B[i][0] = f2acc_get(b0);
-    if (kind == 0) {
-      B[i][1] = C[ci(i, 2)];
-    } else {
-      f2acc b1{0.0f, 0.0f};
-      f2acc_add_mulf(b1, C[ci(i, 0)], c);
-      f2acc_add_mulf(b1, C[ci(i, 1)], sn);
-      B[i][1] = f2acc_get(b1);
-    }
-  }
-  f2acc raa{f.v00, 0.0f}, rab{f.v01, 0.0f}, rbb{f.v11, 0.0f};
-  f2acc_add_mulf(raa, B[0][0], -sn);
-  f2acc_add_mulf(raa, B[1][0], c);
-  f2acc_add_mulf(rab, B[0][1], -sn);
-  f2acc_add_mulf(rab, B[1][1], c);
-  if (kind == 0) {
-    const f2 b = B[2][1];
-    f2acc_add_mulf(rbb, b, 1.0f);
-  } else {
-    f2acc_add_mulf(rbb, B[0][1], c);
-    f2acc_add_mulf(rbb, B[1][1], sn);
-  }
-  const f2 Raa = f2acc_get(raa), Rab = f2acc_get(rab), Rbb = f2acc_get(rbb);
-  f2acc dt{0.0f, 0.0f};
-  f2acc_add_mul(dt, Raa, Rbb);
-  f2acc_add_mul(dt, Rab, f2{-Rab.h, -Rab.l});
-  const f2 idet = f2_recip(f2acc_get(dt));
-  const f2 Waa = f2_mul(Rbb, idet), Wab = f2_mul(f2{-Rab.h, -Rab.l}, idet), Wbb = f2_mul(Raa, idet);
-  // residuals in FP64
-  const double ra = fma(m.s, p[0], -m.c * p[1]);
-  const double rb = kind == 0 ? m.w - p[2] : m.w - fma(m.c, p[0], m.s * p[1]);
-  const f2 ra2 = f2_of(ra), rb2 = f2_of(rb);
-  const float raf = ra2.h, rbf = rb2.h;
-  const float chi2 = fmaf(Waa.h * raf, raf, fmaf(2.0f * Wab.h * raf, rbf, Wbb.h * rbf * rbf));
-  f2 Kg[6][2];
-#pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    f2acc k0{0.0f, 0.0f}, k1{0.0f, 0.0f};
-    f2acc_add_mul(k0, B[i][0], Waa);
-    f2acc_add_mul(k0, B[i][1], Wab);
-    f2acc_add_mul(k1, B[i][0], Wab);
-    f2acc_add_mul(k1, B[i][1], Wbb);
-    Kg[i][0] = f2acc_get(k0);
-    Kg[i][1] = f2acc_get(k1);
-    // the two terms can be large and nearly cancel (early, weakly constrained
-    // updates): the increment is formed in double-float, then widened
-    f2acc dp{0.0f, 0.0f};
-    f2acc_add_mul(dp, Kg[i][0], ra2);
-    f2acc_add_mul(dp, Kg[i][1], rb2);
-    const f2 d = f2acc_get(dp);
-    p[i] += double(d.h) + double(d.l);
-  }
-  p[4] = wrap_phi(p[4]);
-#pragma unroll
-  for (int i = 0; i < 6; ++i)
-#pragma unroll
-    for (int j = 0; j <= i; ++j) {
-      f2acc a = f2acc_of(C[ci(i, j)]);
-      f2acc_add_mul(a, Kg[i][0], f2{-B[j][0].h, -B[j][0].l});
-      f2acc_add_mul(a, Kg[i][1], f2{-B[j][1].h, -B[j][1].l});
-      C[ci(i, j)] = f2acc_get(a);
-    }
-  return double(chi2);
-}
-
 // Inward fit: covariance reset to 100 x the seed-style diagonal, update with
-// the outermost hit in place, then propagate inward hit by hit (state and
-// transport in FP64, covariance in double-float, plain covariance update).
+// the outermost hit in place, then propagate inward hit by hit (FP64, plain
+// covariance update).
 __global__ void k_fit_inward(const GeomDev* __restrict__ g, const float* __restrict__ xyz,
                              const float* __restrict__ lcov, const int* __restrict__ layer, int64_t H,
                              const int* __restrict__ hits, int K, const float* __restrict__ init_par, int64_t NT,
@@ -501,15 +288,14 @@ __global__ void k_fit_inward(const GeomDev* __restrict__ g, const float* __restr
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= NT) return;
   const int* row = hits + t * K;
-  double p[6];
-  f2 C[21];
+  double p[6], C[21];
 #pragma unroll
   for (int k = 0; k < 6; ++k) p[k] = double(init_par[k * NT + t]);
 #pragma unroll
-  for (int k = 0; k < 21; ++k) C[k] = f2{0.0f, 0.0f};
-  C[ci(0, 0)] = C[ci(1, 1)] = C[ci(2, 2)] = f2{1.0f, 0.0f};
-  C[ci(3, 3)] = f2_of(100.0 * (0.05 * p[3]) * (0.05 * p[3]));
-  C[ci(4, 4)] = C[ci(5, 5)] = f2{0.25f, 0.0f};
+  for (int k = 0; k < 21; ++k) C[k] = 0.0;
+  C[ci(0, 0)] = C[ci(1, 1)] = C[ci(2, 2)] = 1.0;
+  C[ci(3, 3)] = 100.0 * (0.05 * p[3]) * (0.05 * p[3]);
+  C[ci(4, 4)] = C[ci(5, 5)] = 0.25;
   const int last = prev_listed(row, K);
   double chi2 = 0.0;
   int ok = 1;
@@ -526,14 +312,14 @@ __global__ void k_fit_inward(const GeomDev* __restrict__ g, const float* __restr
       break;
     }
     const double phi0 = p[4], theta0 = p[5];
-    chi2 += update_inward(f, p, C);
+    chi2 += kf_update<double, false>(f.kind, p, C, f.m);
     turn_by(wrap_phi(p[4] - phi0), p[4], tr.cph, tr.sph);
     turn_by(p[5] - theta0, p[5], tr.cth, tr.sth);
   }
 #pragma unroll
   for (int i = 0; i < 6; ++i) out_par[i * NT + t] = float(p[i]);
 #pragma unroll
-  for (int i = 0; i < 21; ++i) out_cov[i * NT + t] = __fadd_rn(C[i].h, C[i].l);
+  for (int i = 0; i < 21; ++i) out_cov[i * NT + t] = float(C[i]);
   out_chi2[t] = float(chi2);
   if (out_ok) out_ok[t] = ok;
 }

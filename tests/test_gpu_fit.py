@@ -149,3 +149,42 @@ def test_backward_fit_cmslike_mixed_surfaces():
     assert pe.max() < PAR_RTOL
     assert cov_ok(ce, frac=0.9, cap=2e-3)
     ctx.close()
+
+
+def test_backward_fit_built_c2_tracks():
+    """Inward fit of the tracks built on the full C2 event (5000 seeds, 20 %
+    noise hits, so some tracks carry wrong picks with residuals far beyond the
+    hit resolution), in the launch shape the bench times, against the oracle's
+    inward fit of the same hit lists from the same outward result.  Early
+    updates of such tracks move the state far, which is where the two terms of
+    each state increment nearly cancel."""
+    import oracle
+    import paper_2002_06295_gb300 as mkf
+    from _util import gpu_build
+    ev = synth.make_config_event(2)
+    q = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    ev.hit_xyz, ev.hit_lcov = q(ev.hit_xyz), q(ev.hit_lcov)
+    ctx = make_ctx(ev.geom)
+    b = gpu_build(ctx, [ev], max_cands=6)
+    hits = b["hits"]
+    keep = (hits >= 0).sum(1) >= 6
+    hits, sp, sc = hits[keep], q(ev.seed_par[keep]), q(ev.seed_cov[keep])
+    assert keep.sum() > 3000
+    geo = oracle.Geo.of(ev.geom)
+    fpar, fcov, _, fok = oracle.fit(geo, ev.hit_xyz, ev.hit_lcov, ev.hit_layer, hits, sp, sc)
+    fpar = q(fpar)
+    bpar, bcov, _, bok = oracle.fit(geo, ev.hit_xyz, ev.hit_lcov, ev.hit_layer, hits, fpar, fcov, direction=-1)
+    dev = torch.device("cuda", 0)
+    o = mkf.mkf_fit_backward(ctx, f32(ev.hit_xyz.T, dev), f32(ev.hit_lcov.T, dev), i32(ev.hit_layer, dev),
+                             i32(hits, dev), f32(fpar.T, dev))
+    mkf.mkf_sync(ctx)
+    gp = o["par"].cpu().numpy().T.astype(np.float64)
+    gc = o["cov"].cpu().numpy().T.astype(np.float64)
+    good = fok.astype(bool) & bok.astype(bool) & (o["ok"].cpu().numpy() == 1)
+    assert good.mean() > 0.98
+    pe, ce = par_rel_err(gp[good], bpar[good]), cov_rel_err(gc[good], bcov[good])
+    print("built C2 backward fit: %d tracks, par err per parameter" % good.sum(), pe.max(0), "cov err max",
+          ce.max(), "fraction within 1e-4", (ce.max(1) < COV_RTOL).mean())
+    assert pe.max() < PAR_RTOL
+    assert cov_ok(ce, frac=0.9, cap=2e-3)
+    ctx.close()
