@@ -188,3 +188,39 @@ def test_backward_fit_built_c2_tracks():
     assert pe.max() < PAR_RTOL
     assert cov_ok(ce, frac=0.9, cap=2e-3)
     ctx.close()
+
+
+def test_backward_fit_same_in_every_launch_shape():
+    """The inward fit runs one thread per track in blocks of 32, 64 or 128 by
+    track count (the batched workloads take 128): copies of the same tracks
+    give bit-identical results in every shape, and every copy equals the
+    first."""
+    import paper_2002_06295_gb300 as mkf
+    g = synth.geometry_cmslike()
+    rng = np.random.default_rng(15)
+    ev = synth.simulate_event(g, 1500, rng, pt_range=(0.8, 20.0), pt_log=True, eta_max=2.4)
+    keep = (ev.true_hits >= 0).sum(1) >= 6
+    hits, sp, sc = ev.true_hits[keep], ev.seed_par[keep], ev.seed_cov[keep]
+    n = hits.shape[0]
+    dev = torch.device("cuda", 0)
+    ctx = make_ctx(g)
+    X, Lc, Ly = f32(ev.hit_xyz.T, dev), f32(ev.hit_lcov.T, dev), i32(ev.hit_layer, dev)
+    fo = mkf.mkf_fit_tracks(ctx, X, Lc, Ly, i32(hits, dev), f32(sp.T, dev), f32(sc.T, dev))
+    mkf.mkf_sync(ctx)
+    par0 = fo["par"].cpu().numpy().T
+    outs = {}
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    for copies in (1, (n_sm * 64) // n + 1, (n_sm * 128) // n + 1):
+        H = np.tile(hits, (copies, 1))
+        P = np.tile(par0, (copies, 1))
+        o = mkf.mkf_fit_backward(ctx, X, Lc, Ly, i32(H, dev), f32(P.T, dev))
+        mkf.mkf_sync(ctx)
+        outs[copies] = {k: v.cpu().numpy() for k, v in o.items()}
+    base = outs[1]
+    for copies, o in outs.items():
+        for k in ("par", "cov", "chi2", "ok"):
+            a = o[k].reshape(-1, copies * n) if o[k].ndim == 2 else o[k].reshape(1, -1)
+            b = base[k].reshape(-1, n) if base[k].ndim == 2 else base[k].reshape(1, -1)
+            for c in range(copies):
+                assert np.array_equal(a[:, c * n:(c + 1) * n], b, equal_nan=True), (copies, k, c)
+    ctx.close()
