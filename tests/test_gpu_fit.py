@@ -224,3 +224,35 @@ def test_backward_fit_same_in_every_launch_shape():
             for c in range(copies):
                 assert np.array_equal(a[:, c * n:(c + 1) * n], b, equal_nan=True), (copies, k, c)
     ctx.close()
+
+
+def test_forward_fit_same_in_every_launch_shape():
+    """The outward fit's launch shape (blocks of 32, 64 or 128 by track count)
+    leaves every track's result and checkpoints bit-identical."""
+    import paper_2002_06295_gb300 as mkf
+    g, ev, hits, sp, sc, rng = _fit_inputs(1200, seed=16)
+    n, K = hits.shape
+    dev = torch.device("cuda", 0)
+    ctx = make_ctx(g)
+    X, Lc, Ly = f32(ev.hit_xyz.T, dev), f32(ev.hit_lcov.T, dev), i32(ev.hit_layer, dev)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    outs = {}
+    for copies in (1, (n_sm * 64) // n + 1, (n_sm * 128) // n + 1):
+        T = copies * n
+        ckpt = torch.empty((K, 27, T), dtype=torch.float32, device=dev)
+        o = mkf.mkf_fit_tracks(ctx, X, Lc, Ly, i32(np.tile(hits, (copies, 1)), dev), f32(np.tile(sp, (copies, 1)).T, dev),
+                               f32(np.tile(sc, (copies, 1)).T, dev), ckpt=ckpt)
+        mkf.mkf_sync(ctx)
+        r = {k: v.cpu().numpy() for k, v in o.items()}
+        r["ckpt"] = ckpt.cpu().numpy()
+        outs[copies] = r
+    base = outs[1]
+    for copies, o in outs.items():
+        for c in range(copies):
+            cols = slice(c * n, (c + 1) * n)
+            assert np.array_equal(o["par"][:, cols], base["par"], equal_nan=True), copies
+            assert np.array_equal(o["cov"][:, cols], base["cov"], equal_nan=True), copies
+            assert np.array_equal(o["chi2"][cols], base["chi2"], equal_nan=True), copies
+            assert np.array_equal(o["ok"][cols], base["ok"]), copies
+            assert np.array_equal(o["ckpt"][:, :, cols], base["ckpt"], equal_nan=True), copies
+    ctx.close()
