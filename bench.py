@@ -29,6 +29,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOADS = {
+    "c1": "C1 event: 10-cylinder barrel, 100 tracks, 4 candidates/seed, chi2<30, then refit (fwd + adjoint + bwd) "
+          "of every found track",
     "c2": "C2 CMS-like event: 38 surfaces (14 barrel + 24 disk), 5000 tracks, ~85k hits incl. 20% noise, "
           "6 candidates/seed, chi2<30, then refit (fwd + adjoint + bwd) of every found track",
     "c3": "C3 batch: 256 events of the 10-cylinder barrel, 200..8000 tracks/event, 4 candidates/seed, "
@@ -40,7 +42,7 @@ UNIT = "cand-steps/s"
 
 # FP32 work per unit, counted from the kernel formulas as executed (FMA = 2,
 # add/mul/div = 1; sqrt, rsqrt, sin/cos, atan, log not counted); barrel-surface
-# counts, so disk-heavy work is under-counted (see DESIGN.md)
+# counts, so disk-heavy work is under-counted
 FLOPS_NAV_TEST = 44       # one surface tested by the navigation (crossing path + acceptance)
 FLOPS_CAND_STEP = 600     # helix 46 + Jacobian 84 + J C J^T 408 + material 25 + window ~35
 FLOPS_BOX = 7             # one candidate-hit pair examined: residuals r_a, r_b + half-plane test
@@ -137,7 +139,10 @@ def run_reference(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOADS["c2"], "sample": "%d seeds of the event per step" % per_step},
+            "config": {"workload": "C2 CMS-like event: 38 surfaces (14 barrel + 24 disk), 5000 tracks, ~85k hits "
+                                   "incl. 20% noise, 6 candidates/seed, chi2<30; building only (the oracle has no "
+                                   "refit at this scale: its gradient takes one dual-number pass per input)",
+                       "sample": "%d seeds of the event per step" % per_step},
             "impl": "reference",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": "%d seeds x %d steps of the 5000-seed event, brute-force hit search, "
@@ -436,7 +441,7 @@ def measure_seeding(mkf, dev, reps=5):
             ts.append(a.elapsed_time(e))
     mkf.mkf_sync(ctx)
     w = mkf.mkf_get_seed_stats(ctx)
-    fma_peak = mkf.mkf_measure_fp32_peak(ctx)
+    peak = fp32_peak(dev)
     ctx.close()
     ms = min(ts)
     flops = (w["l1_examined"] * FLOPS_SEED_L1 + w["pairs"] * FLOPS_SEED_PAIR + w["l2_examined"] * FLOPS_SEED_L2
@@ -450,10 +455,10 @@ def measure_seeding(mkf, dev, reps=5):
                         % (int(b.hit_off[-1]), int(b.seed_off[-1]), cuts),
             "ms": ms, "events_per_s": b.n_events / (ms * 1e-3), "seeds": int(o["n"]),
             "seeds_per_s": o["n"] / (ms * 1e-3), "work": w,
-            "roofline": {"bound": "alu", "achieved": ach, "peak": fma_peak, "unit": "TFLOP/s",
-                         "frac": ach / fma_peak if fma_peak else None,
+            "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                         "frac": ach / peak,
                          "traffic": profiled_traffic("k_seed_triplets", SEED_SOURCES),
-                         "peak_basis": "FP32 FMA probe on this device (mkf_measure_fp32_peak)"},
+                         "peak_basis": FP32_PEAK_BASIS},
             "cpu_baseline": {"value": ev0.n_hits / cpu_s, "unit": "hits/s", "cores": 1, "kind": "oracle",
                              "sample": "event 0 (%d hits, brute force over all layer-0 x layer-1 pairs)"
                                        % ev0.n_hits,
@@ -494,7 +499,7 @@ def measure_overlaps(mkf, dev, reps=5):
             ts.append(a.elapsed_time(e))
     mkf.mkf_sync(ctx)
     w = mkf.mkf_get_overlap_stats(ctx)
-    fma_peak = mkf.mkf_measure_fp32_peak(ctx)
+    peak = fp32_peak(dev)
     bh, flags, gh = b["hits"].cpu().numpy(), b["flags"].cpu().numpy(), o["hit"].cpu().numpy()
     ctx.close()
     ok = tot = 0
@@ -516,10 +521,10 @@ def measure_overlaps(mkf, dev, reps=5):
                         "%d built tracks; chi2 < 20, box 1 cm (r phi) x 10 cm" % (ev.n_hits, ev.n_seeds),
             "ms": ms, "tracks_per_s": ev.n_seeds / (ms * 1e-3), "work": w,
             "recovered_true_overlaps": ok / tot if tot else None, "true_overlaps_on_kept_tracks": tot,
-            "roofline": {"bound": "alu", "achieved": ach, "peak": fma_peak, "unit": "TFLOP/s",
-                         "frac": ach / fma_peak if fma_peak else None,
+            "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                         "frac": ach / peak,
                          "traffic": profiled_traffic("k_overlaps", OVERLAP_SOURCES),
-                         "peak_basis": "FP32 FMA probe on this device (mkf_measure_fp32_peak)"},
+                         "peak_basis": FP32_PEAK_BASIS},
             "cpu_baseline": {"value": n_s / cpu_s, "unit": "tracks/s", "cores": 1, "kind": "oracle",
                              "sample": "the first %d built tracks (brute force over the layer's hits)" % n_s}}
 
@@ -576,12 +581,254 @@ def rank_reduce(dist, dev, values, op):
     return [float(x) for x in t.tolist()]
 
 
+FP32_PEAK_BASIS = "FP32: SMs x 128 lanes x 2 flop x maximum SM clock (MEASURED_PEAKS.json sm_max_mhz)"
+
+
+def fp32_peak(dev, max_mhz=None):
+    """FP32 CUDA-core peak in TFLOP/s: every SM's 128 FP32 lanes issuing one FMA
+    (2 flop) per clock at the maximum SM clock."""
+    import torch
+    props = torch.cuda.get_device_properties(dev)
+    mhz = max_mhz or measured_peaks().get("sm_max_mhz", 2070.0)
+    return props.multi_processor_count * FP32_LANES * 2 * mhz * 1e6 / 1e12
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return json.load(f)
     except (OSError, ValueError):
         return {}
+
+
+def workload_events(synth, cfg_id, rank=0):
+    """The events of one timed step of a workload (rank r takes its own events)."""
+    if synth.WORKLOAD_SPECS[cfg_id]["n_events"] == 1:
+        return [synth.make_config_event(cfg_id, rank)]
+    return [synth.make_config_event(cfg_id, rank * 10000 + e) for e in range(synth.WORKLOAD_SPECS[cfg_id]["n_events"])]
+
+
+def time_path(mkf, dev, evs, spec, steps, warmup, dist=None, clocks=None, graph=True):
+    """Time the whole path on one batch of events: binning -> building with
+    duplicate removal -> forward fit with checkpoints -> adjoint, beside the
+    inward fit on a side stream.  Inputs are resident in HBM before the timed
+    region; the L2 is flushed between steps.  The step is timed eagerly and as
+    one replayed CUDA graph, and end to end (pinned host inputs copied in,
+    results copied out, inside the timed region).  Times are the slowest
+    rank's; work counters are summed over the ranks."""
+    import numpy as np
+    import torch
+    from paper_2002_06295_gb300 import tune
+    g = evs[0].geom
+    ctx = mkf.Context(dev.index)
+    mkf.mkf_load_geometry(ctx, g.table(), g.bz, 64, 16)
+    f32 = dict(dtype=torch.float32)
+    cat = lambda name: np.concatenate([getattr(e, name) for e in evs], 0)
+    n_hits = int(sum(e.n_hits for e in evs))
+    host = dict(xyz=torch.tensor(cat("hit_xyz").T.copy(), **f32), lcov=torch.tensor(cat("hit_lcov").T.copy(), **f32),
+                layer=torch.tensor(cat("hit_layer"), dtype=torch.int32),
+                hoff=torch.tensor(np.concatenate([[0], np.cumsum([e.n_hits for e in evs])]), dtype=torch.int64),
+                sp=torch.tensor(cat("seed_par").T.copy(), **f32), sc=torch.tensor(cat("seed_cov").T.copy(), **f32),
+                soff=torch.tensor(np.concatenate([[0], np.cumsum([e.n_seeds for e in evs])]), dtype=torch.int64))
+    host = {k: v.pin_memory() for k, v in host.items()}
+    d = {k: v.to(dev) for k, v in host.items()}
+    # launch shape and bin granularity picked on these events (not timed)
+    tuned = tune.autotune_build(ctx, g.table(), g.bz, d["xyz"], d["lcov"], d["layer"], d["hoff"], d["sp"], d["sc"],
+                                d["soff"], max_cands=spec["max_cands"], chi2_cut=spec["chi2_cut"],
+                                max_holes=spec["max_holes"], min_hits=spec["min_hits"], dup_frac=spec["dup_frac"])
+    S, L = int(sum(e.n_seeds for e in evs)), g.n_layers
+    out = mkf.alloc_build_outputs(ctx, S)
+    ckpt = torch.empty((L, 27, S), dtype=torch.float32, device=dev)
+    fit_out = dict(par=torch.empty((6, S), device=dev), cov=torch.empty((21, S), device=dev),
+                   chi2=torch.empty(S, device=dev), ok=torch.empty(S, dtype=torch.int32, device=dev))
+    bwd_out = dict(par=torch.empty((6, S), device=dev), cov=torch.empty((21, S), device=dev),
+                   chi2=torch.empty(S, device=dev), ok=torch.empty(S, dtype=torch.int32, device=dev))
+    g_chi2 = torch.ones(S, device=dev)
+    adj_out = dict(g_hit=torch.empty((3, n_hits), device=dev), g_align=torch.empty((L, 3), device=dev),
+                   g_x0=torch.empty(L, device=dev))
+    stream = torch.cuda.current_stream()
+    mkf.mkf_set_timing(ctx, True)
+    side = torch.cuda.Stream(device=dev)      # the inward fit runs beside the adjoint
+    fwd_done, bwd_done = torch.cuda.Event(), torch.cuda.Event()
+
+    def step(inp):
+        mkf.mkf_bin_hits(ctx, inp["xyz"], inp["lcov"], inp["layer"], inp["hoff"])
+        mkf.mkf_build_tracks(ctx, inp["sp"], inp["sc"], inp["soff"], chi2_cut=spec["chi2_cut"],
+                             max_cands=spec["max_cands"], max_holes=spec["max_holes"], min_hits=spec["min_hits"],
+                             dup_frac=spec["dup_frac"], out=out)
+        mkf.mkf_fit_tracks(ctx, inp["xyz"], inp["lcov"], inp["layer"], out["hits"], inp["sp"], inp["sc"],
+                           ckpt=ckpt, out=fit_out)
+        cur = torch.cuda.current_stream()
+        fwd_done.record(cur)
+        side.wait_event(fwd_done)
+        mkf.mkf_fit_backward(ctx, inp["xyz"], inp["lcov"], inp["layer"], out["hits"], fit_out["par"], out=bwd_out,
+                             stream=side)
+        bwd_done.record(side)
+        mkf.mkf_fit_tracks_adjoint(ctx, inp["xyz"], inp["lcov"], inp["layer"], out["hits"], inp["sp"], inp["sc"],
+                                   ckpt, g_chi2=g_chi2, out=adj_out)
+        cur.wait_event(bwd_done)
+
+    dd_inputs = {k: torch.empty_like(v) for k, v in d.items()}   # device copies of the host inputs (e2e)
+    for k, v in d.items():
+        dd_inputs[k].copy_(v)
+    for _ in range(max(warmup, 3)):
+        step(d)
+    torch.cuda.synchronize()
+    mkf.mkf_sync(ctx)
+    stats = mkf.mkf_get_stats(ctx)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
+
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    tev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    tm_keys = ("build", "bin", "fit", "adjoint", "backward", "dedup")
+    stage = {k: [] for k in tm_keys}
+    for k in range(steps):
+        flush.fill_(float(k))
+        tev[k][0].record(stream)
+        step(d)
+        tev[k][1].record(stream)
+        tm = mkf.mkf_get_timings(ctx)
+        for key in tm_keys:
+            stage[key].append(tm[key])
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    eager_ms = sum(a.elapsed_time(b) for a, b in tev)
+
+    # the same step captured once as a CUDA graph (the library's calls are
+    # stream-ordered and allocate nothing once warm) and replayed
+    graphs, graph_ms, graph_note = {}, None, None
+    if graph:
+        mkf.mkf_set_timing(ctx, False)
+        try:
+            for name, inp in (("dev", d), ("e2e", dd_inputs)):
+                cg = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(cg):
+                    step(inp)
+                graphs[name] = cg
+            for _ in range(3):
+                graphs["dev"].replay()
+            torch.cuda.synchronize()
+        except Exception as exc:   # capture refused: eager numbers stand
+            graphs, graph_note = {}, "%s: %s" % (type(exc).__name__, str(exc).splitlines()[0][:160])
+        ok = int(rank_reduce(dist, dev, [1 if graphs else 0], "min")[0])   # replay only if every rank captured
+        if ok:
+            if dist:
+                dist.barrier()
+            gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            for k in range(steps):
+                flush.fill_(float(k))
+                gev[k][0].record(stream)
+                graphs["dev"].replay()
+                gev[k][1].record(stream)
+            torch.cuda.synchronize()
+            if dist:
+                dist.barrier()
+            graph_ms = sum(a.elapsed_time(b) for a, b in gev)
+        else:
+            graphs = {}
+        mkf.mkf_set_timing(ctx, True)
+        mkf.mkf_sync(ctx)
+    clk = clocks.stop() if clocks else None
+    # every rank takes the slowest rank's times and the same launch mode
+    eager_ms, gm = rank_reduce(dist, dev, [eager_ms, graph_ms if graph_ms is not None else float("inf")], "max")
+    graph_ms = gm if gm < float("inf") else None
+    use_graph = graph_ms is not None and graph_ms < eager_ms
+    total_ms = graph_ms if use_graph else eager_ms
+
+    # end to end through the API with host buffers: H2D inputs, path, D2H results
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    res_host = dict(hits=torch.empty_like(out["hits"], device="cpu").pin_memory(),
+                    par=torch.empty_like(fit_out["par"], device="cpu").pin_memory(),
+                    flags=torch.empty_like(out["flags"], device="cpu").pin_memory(),
+                    chi2=torch.empty_like(fit_out["chi2"], device="cpu").pin_memory())
+    d2h = sum(v.numel() * v.element_size() for v in res_host.values())
+    e2e_ms = []
+    for k in range(steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for kk, v in host.items():
+            dd_inputs[kk].copy_(v, non_blocking=True)
+        if use_graph:
+            graphs["e2e"].replay()
+        else:
+            step(dd_inputs)
+        res_host["hits"].copy_(out["hits"], non_blocking=True)
+        res_host["par"].copy_(fit_out["par"], non_blocking=True)
+        res_host["flags"].copy_(out["flags"], non_blocking=True)
+        res_host["chi2"].copy_(fit_out["chi2"], non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    mkf.mkf_sync(ctx)
+    units = rank_reduce(dist, dev, [stats["cand_steps"]], "sum")[0]
+    e2e_total = rank_reduce(dist, dev, [sum(e2e_ms)], "max")[0]
+    graphs.clear()
+    ctx.close()
+    return dict(steps=steps, units=units, stats=stats, total_ms=total_ms, eager_ms=eager_ms, graph_ms=graph_ms,
+                graph_note=graph_note, use_graph=use_graph, e2e_total_ms=e2e_total, h2d=h2d, d2h=d2h,
+                stage={k: statistics.mean(v) for k, v in stage.items()}, n_events=len(evs), S=S, n_hits=n_hits,
+                L=L, max_cands=spec["max_cands"], tuned={k: tuned[k] for k in ("n_phi", "n_w", "warps", "lanes")},
+                clocks=clk)
+
+
+# kernels of one step: binning 5 (keys, 3-pass scan, scatter), building 1,
+# dedup 3, forward fit 1, adjoint 1, inward fit 1
+LAUNCHES_PER_STEP = 5 + 1 + 3 + 1 + 1 + 1
+
+
+def path_summary(r, workload, dev, max_mhz=None):
+    """Throughput, stage times, end-to-end figure and the building kernel's
+    FP32 roofline of one time_path result."""
+    steps, total_ms = r["steps"], r["total_ms"]
+    st = r["stats"]
+    b_ms = r["stage"]["build"]
+    alg_flops = (st["nav_tests"] * FLOPS_NAV_TEST + st["cand_steps"] * FLOPS_CAND_STEP
+                 + st["chi2_evals"] * FLOPS_BOX + st["chi2_full"] * FLOPS_CHI2 + st["updates"] * FLOPS_UPDATE)
+    achieved = alg_flops / (b_ms * 1e-3) / 1e12
+    peak = fp32_peak(dev, max_mhz)
+    return {
+        "value": r["units"] * steps / (total_ms * 1e-3), "unit": UNIT, "ms_per_step": total_ms / steps,
+        "config": {"workload": WORKLOADS[workload], "events_per_step_per_gpu": r["n_events"], "tracks": r["S"],
+                   "hits": r["n_hits"], "surfaces": r["L"], "max_cands": r["max_cands"],
+                   "l2": "flushed (256 MB write) between timed steps", "adjoint_in_step": True,
+                   "launch": "cuda_graph" if r["use_graph"] else "eager", "tuned": r["tuned"]},
+        "events_per_s": r["n_events"] * steps / (total_ms * 1e-3),
+        "fit_tracks_per_s": r["S"] * steps / (total_ms * 1e-3),
+        "stage_ms": r["stage"],
+        "roofline": {"kernel": "k_build (combinatorial building)", "bound": "alu", "achieved": achieved,
+                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": profiled_traffic("k_build_%s" % workload),
+                     "peak_basis": FP32_PEAK_BASIS, "algorithmic_flops_per_launch": alg_flops,
+                     "build_ms": b_ms},
+        "e2e": {"value": r["units"] * steps / (r["e2e_total_ms"] * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"],
+                "ms_per_step": r["e2e_total_ms"] / steps},
+        "gpu_launches": LAUNCHES_PER_STEP * steps,
+        "launch_ms_per_step": {"eager": r["eager_ms"] / steps,
+                               "cuda_graph": None if r["graph_ms"] is None else r["graph_ms"] / steps,
+                               "graph_note": r["graph_note"]},
+        "work": st,
+    }
+
+
+def c1_latency(r):
+    """C1 is launch-latency bound: the whole path on its one 100-track event in
+    microseconds per event."""
+    steps = r["steps"]
+    return {"workload": WORKLOADS["c1"], "us_per_event": 1e3 * r["total_ms"] / steps,
+            "us_per_event_eager": 1e3 * r["eager_ms"] / steps,
+            "us_per_event_cuda_graph": None if r["graph_ms"] is None else 1e3 * r["graph_ms"] / steps,
+            "us_per_event_e2e": 1e3 * r["e2e_total_ms"] / steps,
+            "launch": "cuda_graph" if r["use_graph"] else "eager", "cand_steps": r["stats"]["cand_steps"],
+            "stage_us": {k: 1e3 * v for k, v in r["stage"].items()}}
 
 
 def main():
@@ -635,227 +882,43 @@ def main():
 
     dev = torch.device("cuda", local)
     cfg_id = {"c2": 2, "c3": 3, "c5": 5}[args.workload]
-    if cfg_id == 2:
-        evs = [synth.make_config_event(2, rank)]
-    else:
-        evs = [synth.make_config_event(cfg_id, rank * 10000 + e) for e in range(synth.WORKLOAD_SPECS[cfg_id]["n_events"])]
-    g = evs[0].geom
-    ctx = mkf.Context(local)
-    mkf.mkf_load_geometry(ctx, g.table(), g.bz, 64, 16)
-    spec = synth.WORKLOAD_SPECS[cfg_id]
-    f32 = dict(dtype=torch.float32)
-    cat = lambda name: np.concatenate([getattr(e, name) for e in evs], 0)
-    n_hits = int(sum(e.n_hits for e in evs))
-    host = dict(xyz=torch.tensor(cat("hit_xyz").T.copy(), **f32), lcov=torch.tensor(cat("hit_lcov").T.copy(), **f32),
-                layer=torch.tensor(cat("hit_layer"), dtype=torch.int32),
-                hoff=torch.tensor(np.concatenate([[0], np.cumsum([e.n_hits for e in evs])]), dtype=torch.int64),
-                sp=torch.tensor(cat("seed_par").T.copy(), **f32), sc=torch.tensor(cat("seed_cov").T.copy(), **f32),
-                soff=torch.tensor(np.concatenate([[0], np.cumsum([e.n_seeds for e in evs])]), dtype=torch.int64))
-    host = {k: v.pin_memory() for k, v in host.items()}
-    d = {k: v.to(dev) for k, v in host.items()}
-    # launch shape and bin granularity picked on this event (not timed)
-    from paper_2002_06295_gb300 import tune
-    tuned = tune.autotune_build(ctx, g.table(), g.bz, d["xyz"], d["lcov"], d["layer"], d["hoff"], d["sp"], d["sc"],
-                                d["soff"], max_cands=spec["max_cands"], chi2_cut=spec["chi2_cut"],
-                                max_holes=spec["max_holes"], min_hits=spec["min_hits"], dup_frac=spec["dup_frac"])
-    S, L = int(sum(e.n_seeds for e in evs)), g.n_layers
-    out = mkf.alloc_build_outputs(ctx, S)
-    ckpt = torch.empty((L, 27, S), dtype=torch.float32, device=dev)
-    fit_out = dict(par=torch.empty((6, S), device=dev), cov=torch.empty((21, S), device=dev),
-                   chi2=torch.empty(S, device=dev), ok=torch.empty(S, dtype=torch.int32, device=dev))
-    bwd_out = dict(par=torch.empty((6, S), device=dev), cov=torch.empty((21, S), device=dev),
-                   chi2=torch.empty(S, device=dev), ok=torch.empty(S, dtype=torch.int32, device=dev))
-    g_chi2 = torch.ones(S, device=dev)
-    adj_out = dict(g_hit=torch.empty((3, n_hits), device=dev), g_align=torch.empty((L, 3), device=dev),
-                   g_x0=torch.empty(L, device=dev))
-    has_adjoint = [True]
-    stream = torch.cuda.current_stream()
-    mkf.mkf_set_timing(ctx, True)
-
-    side = torch.cuda.Stream(device=dev)      # the inward fit runs beside the adjoint
-    fwd_done, bwd_done = torch.cuda.Event(), torch.cuda.Event()
-
-    def step(inp):
-        mkf.mkf_bin_hits(ctx, inp["xyz"], inp["lcov"], inp["layer"], inp["hoff"])
-        mkf.mkf_build_tracks(ctx, inp["sp"], inp["sc"], inp["soff"], chi2_cut=spec["chi2_cut"],
-                             max_cands=spec["max_cands"], max_holes=spec["max_holes"], min_hits=spec["min_hits"],
-                             dup_frac=spec["dup_frac"], out=out)
-        mkf.mkf_fit_tracks(ctx, inp["xyz"], inp["lcov"], inp["layer"], out["hits"], inp["sp"], inp["sc"],
-                           ckpt=ckpt, out=fit_out)
-        cur = torch.cuda.current_stream()
-        fwd_done.record(cur)
-        side.wait_event(fwd_done)
-        mkf.mkf_fit_backward(ctx, inp["xyz"], inp["lcov"], inp["layer"], out["hits"], fit_out["par"], out=bwd_out,
-                             stream=side)
-        bwd_done.record(side)
-        if has_adjoint[0]:
-            try:
-                mkf.mkf_fit_tracks_adjoint(ctx, inp["xyz"], inp["lcov"], inp["layer"], out["hits"], inp["sp"],
-                                           inp["sc"], ckpt, g_chi2=g_chi2, out=adj_out)
-            except mkf.MkfError:
-                has_adjoint[0] = False
-        cur.wait_event(bwd_done)
-
-    dd_inputs = {k: torch.empty_like(v) for k, v in d.items()}   # device copies of the host inputs (e2e)
-    for k, v in d.items():
-        dd_inputs[k].copy_(v)
-    # warm-up
-    for _ in range(max(args.warmup, 3) if args.warmup > 0 else 0):
-        step(d)
-    torch.cuda.synchronize()
-    mkf.mkf_sync(ctx)
-    stats = mkf.mkf_get_stats(ctx)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
-
+    evs = workload_events(synth, cfg_id, rank)
     clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.3)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    tev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    build_ms, bin_ms, fit_ms, adj_ms, bwd_ms, dd_ms = [], [], [], [], [], []
-    for k in range(args.steps):
-        flush.fill_(float(k))
-        tev[k][0].record(stream)
-        step(d)
-        tev[k][1].record(stream)
-        tm = mkf.mkf_get_timings(ctx)
-        build_ms.append(tm["build"]); bin_ms.append(tm["bin"]); fit_ms.append(tm["fit"])
-        adj_ms.append(tm["adjoint"]); bwd_ms.append(tm["backward"]); dd_ms.append(tm["dedup"])
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    step_ms = [a.elapsed_time(b) for a, b in tev]
-    eager_ms = sum(step_ms)
-
-    # the same step captured once as a CUDA graph (the library's calls are
-    # stream-ordered and allocate nothing once warm) and replayed
-    graphs, graph_ms, graph_note = {}, None, None
-    if not args.no_graph:
-        mkf.mkf_set_timing(ctx, False)
-        try:
-            for name, inp in (("dev", d), ("e2e", dd_inputs)):
-                g = torch.cuda.CUDAGraph()
-                with torch.cuda.graph(g):
-                    step(inp)
-                graphs[name] = g
-            for _ in range(3):
-                graphs["dev"].replay()
-            torch.cuda.synchronize()
-        except Exception as exc:   # capture refused: eager numbers stand
-            graphs, graph_note = {}, "%s: %s" % (type(exc).__name__, str(exc).splitlines()[0][:160])
-        ok = int(rank_reduce(dist, dev, [1 if graphs else 0], "min")[0])   # replay only if every rank captured
-        if ok:
-            if dist:
-                dist.barrier()
-            gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                   for _ in range(args.steps)]
-            for k in range(args.steps):
-                flush.fill_(float(k))
-                gev[k][0].record(stream)
-                graphs["dev"].replay()
-                gev[k][1].record(stream)
-            torch.cuda.synchronize()
-            if dist:
-                dist.barrier()
-            graph_ms = sum(a.elapsed_time(b) for a, b in gev)
-        else:
-            graphs = {}
-        mkf.mkf_set_timing(ctx, True)
-        mkf.mkf_sync(ctx)
-    clk = clocks.stop()
-    # every rank takes the slowest rank's times and the same launch mode
-    eager_ms, gm = rank_reduce(dist, dev, [eager_ms, graph_ms if graph_ms is not None else float("inf")], "max")
-    graph_ms = gm if gm < float("inf") else None
-    use_graph = graph_ms is not None and graph_ms < eager_ms
-    total_ms = graph_ms if use_graph else eager_ms
-
-    # end to end through the API with host buffers: H2D inputs, path, D2H results
-    h2d = sum(v.numel() * v.element_size() for v in host.values())
-    res_host = dict(hits=torch.empty_like(out["hits"], device="cpu").pin_memory(),
-                    par=torch.empty_like(fit_out["par"], device="cpu").pin_memory(),
-                    flags=torch.empty_like(out["flags"], device="cpu").pin_memory(),
-                    chi2=torch.empty_like(fit_out["chi2"], device="cpu").pin_memory())
-    d2h = sum(v.numel() * v.element_size() for v in res_host.values())
-    e2e_ms = []
-    dd = dd_inputs
-    for k in range(args.steps):
-        flush.fill_(float(k))
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for kk, v in host.items():
-            dd[kk].copy_(v, non_blocking=True)
-        if use_graph:
-            graphs["e2e"].replay()
-        else:
-            step(dd)
-        res_host["hits"].copy_(out["hits"], non_blocking=True)
-        res_host["par"].copy_(fit_out["par"], non_blocking=True)
-        res_host["flags"].copy_(out["flags"], non_blocking=True)
-        res_host["chi2"].copy_(fit_out["chi2"], non_blocking=True)
-        b.record(stream)
-        b.synchronize()
-        e2e_ms.append(a.elapsed_time(b))
-    mkf.mkf_sync(ctx)
-    # whole-job figures: the work of all ranks over the slowest rank's time
-    units = rank_reduce(dist, dev, [stats["cand_steps"]], "sum")[0]
-    e2e_total = rank_reduce(dist, dev, [sum(e2e_ms)], "max")[0]
-
+    r = time_path(mkf, dev, evs, synth.WORKLOAD_SPECS[cfg_id], args.steps, args.warmup, dist=dist, clocks=clocks,
+                  graph=not args.no_graph)
+    clk = r["clocks"]
     if rank != 0:
         return
     secondary = None
     if world == 1 and not args.no_secondary:
         from paper_2002_06295_gb300 import tune as _tune
-        secondary = {"batched_vs_plain": measure_batched(mkf, _tune, dev),
-                     "fit_gradient": measure_fit_gradient(mkf, dev),
-                     "strip_clustering": measure_strips(mkf, dev),
-                     "seeding": measure_seeding(mkf, dev),
-                     "overlaps": measure_overlaps(mkf, dev)}
-    value = units * args.steps / (total_ms * 1e-3)
-    e2e_value = units * args.steps / (e2e_total * 1e-3)
-    b_ms = statistics.mean(build_ms)
-    alg_flops = (stats["nav_tests"] * FLOPS_NAV_TEST + stats["cand_steps"] * FLOPS_CAND_STEP
-                 + stats["chi2_evals"] * FLOPS_BOX + stats["chi2_full"] * FLOPS_CHI2
-                 + stats["updates"] * FLOPS_UPDATE)
-    achieved = alg_flops / (b_ms * 1e-3) / 1e12
-    props = torch.cuda.get_device_properties(dev)
-    max_mhz = clk.get("sm_max_mhz") or measured_peaks().get("sm_max_mhz", 2070.0)
-    fma_peak = mkf.mkf_measure_fp32_peak(ctx)   # confirms the derived peak on this device
-    peak = props.multi_processor_count * FP32_LANES * 2 * max_mhz * 1e6 / 1e12
-    # binning 5 (keys, 3-pass scan, scatter), building 1, dedup 3, fit 1, adjoint 1, inward fit 1
-    launches_per_step = 5 + 1 + 3 + 1 + (1 if has_adjoint[0] else 0) + 1
+        secondary = {}
+        if args.workload != "c5":
+            secondary["stress_c5"] = path_summary(
+                time_path(mkf, dev, workload_events(synth, 5, 0), synth.WORKLOAD_SPECS[5], min(args.steps, 5), 3),
+                "c5", dev)
+        secondary["c1_event"] = c1_latency(
+            time_path(mkf, dev, workload_events(synth, 1, 0), synth.WORKLOAD_SPECS[1], 50, 5))
+        secondary.update({"batched_vs_plain": measure_batched(mkf, _tune, dev),
+                          "fit_gradient": measure_fit_gradient(mkf, dev),
+                          "strip_clustering": measure_strips(mkf, dev),
+                          "seeding": measure_seeding(mkf, dev),
+                          "overlaps": measure_overlaps(mkf, dev)})
+    summ = path_summary(r, args.workload, dev, clk.get("sm_max_mhz"))
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": summ["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": summ["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload], "events_per_step_per_gpu": len(evs), "tracks": S,
-                   "hits": n_hits,
-                   "surfaces": L, "max_cands": spec["max_cands"], "l2": "flushed (256 MB write) between timed steps",
-                   "adjoint_in_step": has_adjoint[0],
-                   "launch": "cuda_graph" if use_graph else "eager",
-                   "tuned": {k: tuned[k] for k in ("n_phi", "n_w", "warps", "lanes")}},
-        "events_per_s": world * len(evs) * args.steps / (total_ms * 1e-3),
-        "fit_tracks_per_s": world * S * args.steps / (total_ms * 1e-3),
-        "stage_ms": {"bin": statistics.mean(bin_ms), "build": b_ms, "dedup": statistics.mean(dd_ms),
-                     "fit": statistics.mean(fit_ms), "adjoint": statistics.mean(adj_ms) if has_adjoint[0] else None,
-                     "backward": statistics.mean(bwd_ms)},
-        "work": stats,
-        "roofline": {"kernel": "k_build (combinatorial building)", "bound": "alu", "achieved": achieved,
-                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": profiled_traffic("k_build_%s" % args.workload),
-                     "peak_basis": "FP32: %d SMs x %d lanes x 2 x %.0f MHz" % (props.multi_processor_count,
-                                                                               FP32_LANES, max_mhz),
-                     "peak_fma_probe_tflops": fma_peak,
-                     "algorithmic_flops_per_launch": alg_flops},
+        "config": summ["config"],
+        "events_per_s": world * summ["events_per_s"],
+        "fit_tracks_per_s": world * summ["fit_tracks_per_s"],
+        "stage_ms": summ["stage_ms"],
+        "work": r["stats"],
+        "roofline": summ["roofline"],
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "ms_per_step": e2e_total / args.steps},
-        "gpu_launches": launches_per_step * args.steps,
-        "launch_ms_per_step": {"eager": eager_ms / args.steps,
-                               "cuda_graph": None if graph_ms is None else graph_ms / args.steps,
-                               "graph_note": graph_note},
+        "e2e": summ["e2e"],
+        "gpu_launches": summ["gpu_launches"],
+        "launch_ms_per_step": summ["launch_ms_per_step"],
         "secondary": secondary,
         "clocks": clk,
     }

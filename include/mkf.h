@@ -298,13 +298,6 @@ mkf_status mkf_get_stats(mkf_ctx* ctx, int64_t* out, int n, void* stream);
 mkf_status mkf_set_timing(mkf_ctx* ctx, int on);
 mkf_status mkf_get_timings(mkf_ctx* ctx, float* ms, int n, void* stream);
 
-/* FP32 FMA throughput of the context's device in TFLOP/s (HOST output),
- * measured with a kernel of independent FMA chains over every SM (best of two
- * timed launches after a warm-up; synchronises `stream`).  The paper has no
- * counterpart: it confirms the FP32 peak against which the building kernel's
- * roofline fraction is stated. */
-mkf_status mkf_measure_fp32_peak(mkf_ctx* ctx, float* out_tflops, void* stream);
-
 /* Duplicate removal alone on given tracks (same rule as in mkf_build_tracks):
  *   hits [S][L] hit ids (-1 none), score [S], nhits [S], ev_seed_off [E+1]
  *   out_flags [S]  MKF_TRK_*  */
@@ -323,11 +316,15 @@ mkf_status mkf_dedup_tracks(mkf_ctx* ctx, const int* hits, int L, const float* s
  * n_hits_total <= 524288, L <= MKF_MAX_LAYERS; larger inputs return
  * MKF_ERR_CAPACITY and nothing is enqueued.  The first call on a device looks
  * up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  All calls share the
- * array: calls whose work can overlap on the GPU race and must be serialised
- * by the caller.  Device-side problems are written as MKF status bits to
- * out_status (DEVICE int, cleared by the call; may be NULL): 1 capacity,
- * 2 resolution did not converge, 4 an input hit id out of range. */
+ * current; make that first call before any stream capture.  That address is
+ * kept for the life of the process, so it assumes the device's primary context
+ * stays alive: do not call this entry point again after cudaDeviceReset.  All
+ * calls share the array: calls whose work can overlap on the GPU race and must
+ * be serialised by the caller.  Device-side problems are written as MKF status
+ * bits to out_status (DEVICE int, cleared by the call; may be NULL): 1
+ * capacity, 2 resolution did not converge, 4 an input index out of range (a
+ * hit id, or an event offset outside 0..n_seeds, which is clamped into that
+ * range so that nothing is read or written past the track arrays). */
 mkf_status mkf_dedup_tracks_noalloc(const int* hits, int L, const float* score, const int* nhits,
                                     const int64_t* ev_seed_off, int n_events, int64_t n_seeds, int64_t n_hits_total,
                                     int min_hits, float dup_frac, int* out_flags, int* out_status, void* stream);

@@ -321,8 +321,13 @@ template <class T> bool same_side(const T p[6], const Meas<T>& m) {
   return val(m.c) * val(p[0]) + val(m.s) * val(p[1]) > 0;
 }
 
-// Predicted chi2 with R = V + H C H^T; when apply: K = C H^T R^-1,
-// p += K r, C -= K R K^T (formed as B R^-1 B^T with B = C H^T).
+// Predicted chi2 with R = V + H C H^T; when apply: K = C H^T R^-1, p += K r,
+// and the updated covariance C' = C - K R K^T written in Joseph form,
+// C' = (I - K H) C (I - K H)^T + K V K^T.  The two are the same matrix (expand
+// the Joseph form with K R = C H^T); the Joseph form is a sum of two positive
+// semi-definite terms, so rounding cannot make C' indefinite, which the
+// difference C - K R K^T can on ill-conditioned measurements (a strip disk
+// with sigma_r / sigma_rphi = 333).
 template <class T> T kf_update(T p[6], T C[21], const Meas<T>& m, bool apply) {
   T H[2][6];
   for (int k = 0; k < 6; ++k) H[0][k] = H[1][k] = T(0.0);
@@ -369,8 +374,29 @@ template <class T> T kf_update(T p[6], T C[21], const Meas<T>& m, bool apply) {
     for (int a = 0; a < 2; ++a) K[i][a] = B[i][0] * W[0][a] + B[i][1] * W[1][a];
   for (int i = 0; i < 6; ++i) p[i] = p[i] + K[i][0] * res[0] + K[i][1] * res[1];
   p[4] = wrap_phi(p[4]);
+  // A = I - K H
+  T A[6][6];
   for (int i = 0; i < 6; ++i)
-    for (int j = 0; j <= i; ++j) C[ci(i, j)] = C[ci(i, j)] - (K[i][0] * B[j][0] + K[i][1] * B[j][1]);
+    for (int j = 0; j < 6; ++j) A[i][j] = T(i == j ? 1.0 : 0.0) - (K[i][0] * H[0][j] + K[i][1] * H[1][j]);
+  // AC = A C, then C' = AC A^T + K V K^T
+  T AC[6][6];
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) {
+      T acc = T(0.0);
+      for (int k = 0; k < 6; ++k) acc = acc + A[i][k] * C[ci(k, j)];
+      AC[i][j] = acc;
+    }
+  const double V[2][2] = {{m.v00, m.v01}, {m.v01, m.v11}};
+  T Cn[21];
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j <= i; ++j) {
+      T acc = T(0.0);
+      for (int k = 0; k < 6; ++k) acc = acc + AC[i][k] * A[j][k];
+      for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) acc = acc + K[i][a] * V[a][b] * K[j][b];
+      Cn[ci(i, j)] = acc;
+    }
+  for (int k = 0; k < 21; ++k) C[k] = Cn[k];
   return chi2;
 }
 

@@ -31,7 +31,6 @@ SIGNATURES = {
     "mkf_get_stats": (i32, [P, P, i32, P]),
     "mkf_set_timing": (i32, [P, i32]),
     "mkf_get_timings": (i32, [P, P, i32, P]),
-    "mkf_measure_fp32_peak": (i32, [P, P, P]),
     "mkf_set_strip_config": (i32, [P, i32, i32, i32]),
     "mkf_seed_tracks": (i32, [P, f32, f32, f32, f32, i64, P, P, P, P, P]),
     "mkf_get_seed_stats": (i32, [P, P, i32, P]),

@@ -297,13 +297,6 @@ def mkf_get_seed_stats(ctx, stream=None):
     return {k: int(buf[i]) for i, k in enumerate(SEED_STAT_NAMES)}
 
 
-def mkf_measure_fp32_peak(ctx, stream=None):
-    v = (ctypes.c_float * 1)()
-    ctx._check(ctx.lib.mkf_measure_fp32_peak(ctx.h, ctypes.cast(v, ctypes.c_void_p), _stream(stream)),
-               "mkf_measure_fp32_peak")
-    return float(v[0])
-
-
 def mkf_dedup_tracks(ctx, hits, score, nhits, ev_seed_off, n_hits_total, min_hits=4, dup_frac=0.5, out_flags=None,
                      stream=None):
     S, L = int(hits.shape[0]), int(hits.shape[1])

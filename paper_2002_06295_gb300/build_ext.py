@@ -16,7 +16,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build", platform.machine())
 LIB = os.path.join(HERE, "libmkf.so")
 LIB_ARCH = LIB + ".arch"   # machine the library was linked for
-SOURCES = ["abi.cu", "bin_hits.cu", "build.cu", "dedup.cu", "fit.cu", "fit_adjoint.cu", "overlaps.cu", "probe.cu", "seeds.cu", "strips.cu"]
+SOURCES = ["abi.cu", "bin_hits.cu", "build.cu", "dedup.cu", "fit.cu", "fit_adjoint.cu", "overlaps.cu", "seeds.cu", "strips.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "--expt-relaxed-constexpr"]
 

@@ -58,7 +58,7 @@ void mkf_destroy(mkf_ctx* ctx) {
                     &ctx->bin_cnt,  &ctx->keys,    &ctx->ranks,     &ctx->vmax,     &ctx->ev_hit_off,
                     &ctx->scan_part, &ctx->seed_ctr, &ctx->stats,    &ctx->status,   &ctx->dd_head,
                     &ctx->dd_next,  &ctx->dd_beat, &ctx->dd_nbeat,  &ctx->dd_state, &ctx->track_hits,
-                    &ctx->probe_buf, &ctx->strip_bits, &ctx->seed_cnt, &ctx->seed_off, &ctx->seed_part, &ctx->seed_pairs,
+                    &ctx->strip_bits, &ctx->seed_cnt, &ctx->seed_off, &ctx->seed_part, &ctx->seed_pairs,
                     &ctx->seed_qcnt, &ctx->seed_qoff, &ctx->grid_key, &ctx->grid_rank, &ctx->grid_cnt,
                     &ctx->grid_off, &ctx->grid_rec, &ctx->seed_stats, &ctx->ovl_stats,
                     &ctx->seed_scratch, &ctx->seed_loc};

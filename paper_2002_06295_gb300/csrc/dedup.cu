@@ -90,12 +90,18 @@ __global__ void k_dd_conflicts(const int* __restrict__ hits, int L, const float*
   if (overflow) atomicOr(status, kStatCapacity);
 }
 
-// state: 0 undecided, 1 kept, 2 duplicate, 3 short
-__global__ void k_dd_resolve(const int64_t* __restrict__ ev_seed_off, const int* __restrict__ nhits, int min_hits,
-                             const int* __restrict__ beat, const int* __restrict__ nbeat, int* state,
+// state: 0 undecided, 1 kept, 2 duplicate, 3 short.  The event offsets come
+// from the caller's device memory: they are clamped to [0, n_seeds] (and the
+// end to no less than the start) so that a wrong offset can never index past
+// the track arrays; clamping sets the bad-input status bit.  stats may be NULL.
+__global__ void k_dd_resolve(const int64_t* __restrict__ ev_seed_off, int64_t n_seeds, const int* __restrict__ nhits,
+                             int min_hits, const int* __restrict__ beat, const int* __restrict__ nbeat, int* state,
                              int* __restrict__ out_flags, unsigned long long* __restrict__ stats,
                              int* __restrict__ status) {
-  const int64_t s0 = ev_seed_off[blockIdx.x], s1 = ev_seed_off[blockIdx.x + 1];
+  const int64_t r0 = ev_seed_off[blockIdx.x], r1 = ev_seed_off[blockIdx.x + 1];
+  const int64_t s0 = r0 < 0 ? 0 : (r0 > n_seeds ? n_seeds : r0);
+  const int64_t s1 = r1 < s0 ? s0 : (r1 > n_seeds ? n_seeds : r1);
+  if ((s0 != r0 || s1 != r1) && threadIdx.x == 0) atomicOr(status, kStatBadInput);
   for (int64_t a = s0 + threadIdx.x; a < s1; a += blockDim.x) state[a] = nhits[a] >= min_hits ? 0 : 3;
   __syncthreads();
   volatile int* vs = state;
@@ -140,7 +146,7 @@ __global__ void k_dd_resolve(const int64_t* __restrict__ ev_seed_off, const int*
     if (st == 0) atomicOr(status, kStatTimeout);
   }
   for (int o = 16; o > 0; o >>= 1) kept += __shfl_xor_sync(0xffffffffu, kept, o);
-  if ((threadIdx.x & 31) == 0 && kept) atomicAdd(&stats[3], kept);
+  if (stats && (threadIdx.x & 31) == 0 && kept) atomicAdd(&stats[3], kept);
 }
 
 }  // namespace
@@ -167,7 +173,7 @@ cudaError_t launch_dedup(mkf_ctx* ctx, const int* hits, int L, const float* scor
   k_dd_conflicts<<<gs, T, 0, st>>>(hits, L, score, nhits, n_seeds, n_hits_total, min_hits, dup_frac,
                                    ctx->dd_head.as<int>(), ctx->dd_next.as<int>(), ctx->dd_beat.as<int>(),
                                    ctx->dd_nbeat.as<int>(), status);
-  k_dd_resolve<<<(unsigned)n_events, 1024, 0, st>>>(ev_seed_off, nhits, min_hits, ctx->dd_beat.as<int>(),
+  k_dd_resolve<<<(unsigned)n_events, 1024, 0, st>>>(ev_seed_off, n_seeds, nhits, min_hits, ctx->dd_beat.as<int>(),
                                                     ctx->dd_nbeat.as<int>(), ctx->dd_state.as<int>(), out_flags,
                                                     ctx->stats.as<unsigned long long>(), status);
   ctx->tock(kTDedup, st);
@@ -211,7 +217,10 @@ int* g_na_ptr[kNaMaxDevices] = {};
 
 // Device address of g_dedup_scratch on the current device, looked up once per
 // device (the host-side symbol is only a stand-in and must not be passed to a
-// kernel).
+// kernel).  The address is cached for the life of the process: it assumes the
+// device's primary context stays alive.  After cudaDeviceReset (or anything
+// else that destroys and recreates the primary context) the cached address is
+// stale, so this entry point must not be called again in that process.
 cudaError_t noalloc_scratch(int** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -248,8 +257,9 @@ extern "C" mkf_status mkf_dedup_tracks_noalloc(const int* hits, int L, const flo
   int* beat = next + kNaNext;
   int* nbeat = beat + kNaBeat;
   int* state = nbeat + kNaMaxSeeds;
-  unsigned long long* stats = reinterpret_cast<unsigned long long*>(state + kNaMaxSeeds);   // 8 counters
-  int* status = out_status ? out_status : reinterpret_cast<int*>(stats + 8);
+  // status word used when the caller passes none (the kept-track counter of the
+  // context path is not kept here: no shared counter grows across calls)
+  int* status = out_status ? out_status : state + kNaMaxSeeds;
   // the array keeps the previous call's contents: reset what must start fresh
   if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return MKF_ERR_CUDA;
   if (n_seeds == 0) return MKF_OK;
@@ -260,7 +270,7 @@ extern "C" mkf_status mkf_dedup_tracks_noalloc(const int* hits, int L, const flo
   k_dd_link<<<gs, T, 0, st>>>(hits, L, nhits, n_seeds, n_hits_total, min_hits, head, next, status);
   k_dd_conflicts<<<gs, T, 0, st>>>(hits, L, score, nhits, n_seeds, n_hits_total, min_hits, dup_frac, head, next, beat,
                                    nbeat, status);
-  k_dd_resolve<<<(unsigned)n_events, 1024, 0, st>>>(ev_seed_off, nhits, min_hits, beat, nbeat, state, out_flags,
-                                                    stats, status);
+  k_dd_resolve<<<(unsigned)n_events, 1024, 0, st>>>(ev_seed_off, n_seeds, nhits, min_hits, beat, nbeat, state,
+                                                    out_flags, nullptr, status);
   return cudaGetLastError() == cudaSuccess ? MKF_OK : MKF_ERR_CUDA;
 }

@@ -61,6 +61,60 @@ def test_noalloc_matches_context_dedup_twice_in_a_row():
     ctx.close()
 
 
+def test_noalloc_calls_allocate_no_device_memory():
+    """The property the entry point exists for: once the outputs exist, further
+    calls leave the device's free memory unchanged (no cudaMalloc inside)."""
+    import paper_2002_06295_gb300 as mkf
+    dev = torch.device("cuda", 0)
+    _, inputs = _track_lists()
+    hits, score, nh, soff, H = inputs[1]
+    hd, sd, nd, od = i32(hits, dev), f32(score, dev), i32(nh, dev), i64(soff, dev)
+    flags = torch.empty(hits.shape[0], dtype=torch.int32, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    assert mkf.mkf_dedup_tracks_noalloc(hd, sd, nd, od, H, out_flags=flags, out_status=status) == 0
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info(dev)[0]
+    for _ in range(5):
+        assert mkf.mkf_dedup_tracks_noalloc(hd, sd, nd, od, H, out_flags=flags, out_status=status) == 0
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info(dev)[0] == free0
+    assert int(status.item()) == 0
+
+
+def test_event_offsets_past_the_tracks_are_clamped():
+    """An over-long last event offset (S + 5 for S tracks) must not make either
+    entry point read or write past the track arrays: both flag it as bad input
+    and still give the flags of the correct offsets for the S tracks."""
+    import paper_2002_06295_gb300 as mkf
+    dev = torch.device("cuda", 0)
+    geom, inputs = _track_lists()
+    hits, score, nh, soff, H = inputs[1]
+    S = hits.shape[0]
+    hd, sd, nd = i32(hits, dev), f32(score, dev), i32(nh, dev)
+    ctx = make_ctx(geom)
+    ref = mkf.mkf_dedup_tracks(ctx, hd, sd, nd, i64(soff, dev), H)
+    mkf.mkf_sync(ctx)
+    bad_off = np.array(soff, np.int64)
+    bad_off[-1] = S + 5
+    flags_ctx = mkf.mkf_dedup_tracks(ctx, hd, sd, nd, i64(bad_off, dev), H)
+    with pytest.raises(mkf.MkfError) as err:
+        mkf.mkf_sync(ctx)
+    assert err.value.code == -1   # MKF_ERR_ARG: an input index out of range
+    assert torch.equal(flags_ctx, ref)
+    flags = torch.full((S,), -7, dtype=torch.int32, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    rc = mkf.mkf_dedup_tracks_noalloc(hd, sd, nd, i64(bad_off, dev), H, out_flags=flags, out_status=status)
+    torch.cuda.synchronize()
+    assert rc == 0
+    assert int(status.item()) & 4
+    assert torch.equal(flags, ref)
+    # the next call with correct offsets starts clean
+    rc = mkf.mkf_dedup_tracks_noalloc(hd, sd, nd, i64(soff, dev), H, out_flags=flags, out_status=status)
+    torch.cuda.synchronize()
+    assert rc == 0 and int(status.item()) == 0 and torch.equal(flags, ref)
+    ctx.close()
+
+
 def test_noalloc_rejects_sizes_beyond_its_array():
     import paper_2002_06295_gb300 as mkf
     dev = torch.device("cuda", 0)
