@@ -13,9 +13,11 @@
 // GB300 mapping:
 //  * a seed is owned by a group of GS consecutive lanes of a warp (GS a power
 //    of two >= N = max_cands, chosen per workload); lane k < N of the group
-//    holds candidate slot k (27 floats in registers) for navigation,
-//    propagation, J C J^T and material; the propagated state and the search
-//    window go to shared memory, the pre-step state stays in registers;
+//    holds candidate slot k (6 parameters and the 21 floats of its covariance's
+//    U-D factors, mkf_ud.cuh, in registers) for navigation, propagation,
+//    the factors' transport with material; the propagated state, its position
+//    covariance and the search window go to shared memory, the pre-step state
+//    stays in registers;
 //  * the whole warp scans the windows of all its candidates together: the phi
 //    rows of the windows, then the hits of those rows, are dealt to the 32
 //    lanes, and each lane's next hit record is copied to shared memory
@@ -34,15 +36,18 @@
 //    walked back once per seed.
 #include "mkf_device.cuh"
 #include "mkf_internal.h"
+#include "mkf_ud.cuh"
 
 namespace mkf {
 
 namespace {
 
 constexpr int kMaxWarps = 8;
-// per-lane shared slot: p[6], C[21], score, nh, nholes|layer, rho, zeta (+1 pad: an odd stride puts
-// the same word of different lanes in different banks)
-constexpr int kSlotWords = 33;
+// per-lane shared slot: p[6], U-D factors[21] (u[15], d[6]), score, nh,
+// nholes|layer, rho, zeta, position covariance (xx, yx, yy, zx, zy, zz) (+1
+// pad: an odd stride puts the same word of different lanes in different banks)
+constexpr int kSlotWords = 39;
+constexpr int kSlotPos = 32;   // first word of the position covariance
 // per-lane window: kind, base bin, nphi, nw, b0, nb, iw0, iw1, ha, hb, hit base (+2 pad, odd stride)
 constexpr int kWinWords = 13;
 constexpr uint32_t kHoleKey = 0x0FFFFFFFu;
@@ -111,45 +116,6 @@ __device__ __forceinline__ void top_insert(unsigned long long* ts, int n, unsign
     if (old == ~0ull) return;
     k = old > k ? old : k;
   }
-}
-
-// C' = J C J^T (+ multiple scattering on C'_phiphi, C'_thetatheta) written to
-// dst[21] without touching C: the candidate keeps its pre-step state in
-// registers, which is the state a candidate that finishes here is stored with.
-// The position block of C' (xx, yx, yy, zz) is also returned for the window.
-__device__ __forceinline__ void transport_cov_into(const Jac4<float>& J, const float C[21], float ms_phi,
-                                                   float ms_theta, float* dst, float cpos[4]) {
-  constexpr int R[4] = {0, 1, 2, 4};
-  float T4[4][6];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 6; ++j) {
-      float acc = 0.0f;
-#pragma unroll
-      for (int k = 0; k < 6; ++k) acc = fmaf(J.r[i][k], C[ci(k, j)], acc);
-      T4[i][j] = acc;
-    }
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    dst[ci(3, R[i])] = T4[i][3];
-    dst[ci(5, R[i])] = T4[i][5];
-#pragma unroll
-    for (int j = 0; j <= i; ++j) {
-      float acc = 0.0f;
-#pragma unroll
-      for (int k = 0; k < 6; ++k) acc = fmaf(T4[i][k], J.r[j][k], acc);
-      if (i == 3 && j == 3) acc += ms_phi;
-      dst[ci(R[i], R[j])] = acc;
-      if (i == 0 && j == 0) cpos[0] = acc;
-      if (i == 1 && j == 0) cpos[1] = acc;
-      if (i == 1 && j == 1) cpos[2] = acc;
-      if (i == 2 && j == 2) cpos[3] = acc;
-    }
-  }
-  dst[ci(3, 3)] = C[ci(3, 3)];
-  dst[ci(5, 3)] = C[ci(5, 3)];
-  dst[ci(5, 5)] = C[ci(5, 5)] + ms_theta;
 }
 
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
@@ -285,7 +251,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
   int hit_base = 0, ebin = 0;
   // per-lane candidate
   bool active = false;
-  float p[6], C[21];
+  float p[6];
+  UD6 u;
   float score = 0.f, rho = 0.f, zeta = 0.f;
   int nh = 0, nholes = 0;
 
@@ -308,8 +275,10 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
         const int64_t S = a.n_seeds;
 #pragma unroll
         for (int k = 0; k < 6; ++k) p[k] = a.seed_par[k * S + seed];
+        float C[21];
 #pragma unroll
         for (int k = 0; k < 21; ++k) C[k] = a.seed_cov[k * S + seed];
+        ud_from_cov(C, u);
         score = 0.f;
         nh = nholes = 0;
         rho = sqrtf(fmaf(p[0], p[0], p[1] * p[1]));
@@ -330,8 +299,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
     ++n_chi2;
     if (hit_in_box(kind, ps[0], ps[1], ps[2], hr, __int_as_float(wd[8]), __int_as_float(wd[9]))) {
       ++n_full;
-      const PosState q{ps[0], ps[1], ps[2], ps[6 + ci(0, 0)], ps[6 + ci(1, 0)], ps[6 + ci(1, 1)],
-                       ps[6 + ci(2, 0)], ps[6 + ci(2, 1)], ps[6 + ci(2, 2)]};
+      const PosState q{ps[0], ps[1], ps[2], ps[kSlotPos], ps[kSlotPos + 1], ps[kSlotPos + 2],
+                       ps[kSlotPos + 3], ps[kSlotPos + 4], ps[kSlotPos + 5]};
       const float chi2 = hit_chi2(kind, q, hr, cut);
       if (chi2 < cut) {
         cnt[ow * 32 + cc] = 1;   // the candidate has a child (only "none" is tested)
@@ -456,8 +425,33 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
         ms_theta = highland_theta0_sq(kind, ly.x0, h.x, h.y, h.cphi, h.sphi, p[3], sin_t, cos_t);
         ms_phi = ms_theta / (sin_t * sin_t);
       }
-      float cpos[4];
-      transport_cov_into(J, C, ms_phi, ms_theta, myprop + 6, cpos);
+      // The transported factors go to shared memory and the candidate keeps its
+      // pre-step factors in registers (the state a candidate that finishes
+      // here is stored with).  To free registers during the transport, the
+      // pre-step factors wait in the slot, the transport runs in place, and
+      // the two are then swapped word by word.
+#pragma unroll
+      for (int k = 0; k < 15; ++k) myprop[6 + k] = u.u[k];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) myprop[21 + k] = u.d[k];
+      ud_transport(J, u, ms_phi, ms_theta);
+      float cp6[6];
+      ud_pos_block(u, cp6);
+#pragma unroll
+      for (int k = 0; k < 15; ++k) {
+        const float t = myprop[6 + k];
+        myprop[6 + k] = u.u[k];
+        u.u[k] = t;
+      }
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        const float t = myprop[21 + k];
+        myprop[21 + k] = u.d[k];
+        u.d[k] = t;
+      }
+#pragma unroll
+      for (int k = 0; k < 6; ++k) myprop[kSlotPos + k] = cp6[k];
+      const float cpos[4] = {cp6[0], cp6[1], cp6[2], cp6[5]};
       const float rc = sqrtf(fmaf(h.x, h.x, h.y * h.y));
       // conservative window: |r_i| < sqrt(cut R_ii) (Cauchy-Schwarz), R_ii bounded
       // by the largest eigenvalue of C_xy (or C_zz) plus the layer's largest hit variance
@@ -628,8 +622,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
         if (nb <= 0) continue;
         const int kind = wd[0], base = wd[1], nphi = wd[2], nw = wd[3], b0 = wd[4], iw0 = wd[6], iw1 = wd[7];
         const float* ps = gprop + c * kSlotWords;
-        const PosState q{ps[0], ps[1], ps[2], ps[6 + ci(0, 0)], ps[6 + ci(1, 0)], ps[6 + ci(1, 1)],
-                         ps[6 + ci(2, 0)], ps[6 + ci(2, 1)], ps[6 + ci(2, 2)]};
+        const PosState q{ps[0], ps[1], ps[2], ps[kSlotPos], ps[kSlotPos + 1], ps[kSlotPos + 2],
+                         ps[kSlotPos + 3], ps[kSlotPos + 4], ps[kSlotPos + 5]};
         const int lbase = base - ebin;
         const int beg = __ldg(&a.bin_off[base]);
         const int end = __ldg(&a.bin_off[base + nphi * nw]);
@@ -663,7 +657,9 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
 #pragma unroll
           for (int k = 0; k < 6; ++k) best[k] = p[k];
 #pragma unroll
-          for (int k = 0; k < 21; ++k) best[6 + k] = C[k];
+          for (int k = 0; k < 15; ++k) best[6 + k] = u.u[k];
+#pragma unroll
+          for (int k = 0; k < 6; ++k) best[21 + k] = u.d[k];
           best[27] = score;
           best[28] = __int_as_float(nh);
           best[29] = __int_as_float(nholes);
@@ -682,7 +678,9 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
 #pragma unroll
       for (int k = 0; k < 6; ++k) p[k] = ps[k];
 #pragma unroll
-      for (int k = 0; k < 21; ++k) C[k] = ps[6 + k];
+      for (int k = 0; k < 15; ++k) u.u[k] = ps[6 + k];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) u.d[k] = ps[21 + k];
       nh = __float_as_int(ps[28]);
       const int packed = __float_as_int(ps[29]);
       nholes = packed & 0xFFFF;
@@ -693,7 +691,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
       uint32_t hloc = kHistHole;
       if (hk != kHoleKey) {
         const HitRec hr = load_rec(a.rec_orig, hit_base + (int)hk);
-        kf_update(G.L[lay].kind, p, C, hr);
+        const Meas<float> m{hr.c, hr.s, hr.w, hr.v00, hr.v01, hr.v11};
+        ud_update(G.L[lay].kind, p, u, m);
         ++nh;
         ++n_upd;
         hloc = hk;
@@ -712,11 +711,17 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
       const int64_t S = a.n_seeds;
       const int last = __float_as_int(best[30]);
       const int bslot = __float_as_int(best[31]);
-      for (int k = li; k < 27; k += GS) {
-        if (k < 6)
-          a.out_par[k * S + seed] = best[k];
-        else
-          a.out_cov[(k - 6) * S + seed] = best[k];
+      for (int k = li; k < 6; k += GS) a.out_par[k * S + seed] = best[k];
+      if (li == 0) {
+        UD6 fb;
+#pragma unroll
+        for (int k = 0; k < 15; ++k) fb.u[k] = best[6 + k];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) fb.d[k] = best[21 + k];
+        float Cb[21];
+        ud_to_cov(fb, Cb);
+#pragma unroll
+        for (int k = 0; k < 21; ++k) a.out_cov[k * S + seed] = Cb[k];
       }
       if (li == 0) {
         const int bnh = __float_as_int(best[28]);

@@ -2,61 +2,75 @@
 // the KF procedure to all hits found in building), outward and inward.
 // One thread per track; the state stays in registers for all its hits.
 //
-// The outward fit runs in FP32.  The inward fit starts from a prior 100 times
-// wider than the seed's, so its first updates shrink variances by factors up
-// to 1e5, and on mixed barrel/disk tracks the state keeps correlations close
-// to 1 for many hits: FP32 cannot carry its covariance to 1e-4, so the inward
-// fit runs in FP64.
+// The outward fit runs in FP32 with the covariance in U-D factorised form
+// (mkf_ud.cuh), which keeps the small conditional variances that pixel hits
+// and strip disks leave.  The inward fit starts from a prior 100 times wider
+// than the seed's, so its first updates shrink variances by factors up to 1e5
+// and, on built tracks that carry wrong picks, move the state by hundreds of
+// standard deviations: an FP32 state (with U-D factors) then ends up to 0.3 of
+// its curvature away from FP64, so the inward fit runs in FP64.
 #include "mkf_device.cuh"
 #include "mkf_fit_common.cuh"
+#include "mkf_ud.cuh"
 #include "mkf_internal.h"
 
 namespace mkf {
 
 namespace {
 
-template <class T>
-__global__ void k_fit(const GeomDev* __restrict__ g, const float* __restrict__ xyz,
-                      const float* __restrict__ lcov, const int* __restrict__ layer, int64_t H,
-                      const int* __restrict__ hits, int K, const float* __restrict__ init_par,
-                      const float* __restrict__ init_cov, int64_t NT, const float* __restrict__ align,
-                      const float* __restrict__ x0, float* __restrict__ out_par, float* __restrict__ out_cov,
-                      float* __restrict__ out_chi2, int* __restrict__ out_ok, float* __restrict__ ckpt) {
+__global__ void k_fit(const GeomDev* __restrict__ g, const float* __restrict__ xyz, const float* __restrict__ lcov,
+                      const int* __restrict__ layer, int64_t H, const int* __restrict__ hits, int K,
+                      const float* __restrict__ init_par, const float* __restrict__ init_cov, int64_t NT,
+                      const float* __restrict__ align, const float* __restrict__ x0, float* __restrict__ out_par,
+                      float* __restrict__ out_cov, float* __restrict__ out_chi2, int* __restrict__ out_ok,
+                      float* __restrict__ ckpt) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= NT) return;
-  const T ck = T(g->c_kappa);
-  T p[6], C[21];
+  const float ck = g->c_kappa;
+  float p[6], C[21];
 #pragma unroll
-  for (int k = 0; k < 6; ++k) p[k] = T(init_par[k * NT + t]);
-  T chi2(0.0);
+  for (int k = 0; k < 6; ++k) p[k] = init_par[k * NT + t];
+#pragma unroll
+  for (int k = 0; k < 21; ++k) C[k] = init_cov[k * NT + t];
+  UD6 u;
+  ud_from_cov(C, u);
+  float chi2 = 0.0f;
   int ok = 1;
   const int* row = hits + t * K;
-#pragma unroll
-  for (int k = 0; k < 21; ++k) C[k] = T(init_cov[k * NT + t]);
   for (int k = 0; k < K; ++k) {
     if (ckpt) {
+      // the adjoint recomputes each step from the state before it, in the
+      // plain covariance form: checkpoint k holds p and C = U D U^T
       float* c = ckpt + (size_t)k * 27 * NT + t;
 #pragma unroll
-      for (int i = 0; i < 6; ++i) c[i * NT] = float(p[i]);
+      for (int i = 0; i < 6; ++i) c[i * NT] = p[i];
+      if (k == 0) {
 #pragma unroll
-      for (int i = 0; i < 21; ++i) c[(6 + i) * NT] = float(C[i]);
+        for (int i = 0; i < 21; ++i) c[(6 + i) * NT] = init_cov[i * NT + t];
+      } else {
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+#pragma unroll
+          for (int j = 0; j <= i; ++j) c[(6 + ci(i, j)) * NT] = ud_cov_entry(u, i, j);
+      }
     }
-    FitHit<T> f;
+    FitHit<float> f;
     if (!load_fit_hit(g, xyz, lcov, layer, H, row[k], align, x0, f)) continue;
-    if (!step_to(f, p, C, ck, +1)) {
+    if (!step_to_ud(f, p, u, ck, +1)) {
       ok = 0;
       // mark the steps that did not happen (x = NaN) for the adjoint
       if (ckpt)
         for (int k2 = k; k2 < K; ++k2) ckpt[(size_t)k2 * 27 * NT + t] = __int_as_float(0x7fc00000);
       break;
     }
-    chi2 += kf_update(f.kind, p, C, f.m);
+    chi2 += ud_update(f.kind, p, u, f.m);
   }
 #pragma unroll
-  for (int k = 0; k < 6; ++k) out_par[k * NT + t] = float(p[k]);
+  for (int k = 0; k < 6; ++k) out_par[k * NT + t] = p[k];
+  ud_to_cov(u, C);
 #pragma unroll
-  for (int k = 0; k < 21; ++k) out_cov[k * NT + t] = float(C[k]);
-  out_chi2[t] = float(chi2);
+  for (int k = 0; k < 21; ++k) out_cov[k * NT + t] = C[k];
+  out_chi2[t] = chi2;
   if (out_ok) out_ok[t] = ok;
 }
 
@@ -338,7 +352,7 @@ cudaError_t launch_fit(mkf_ctx* ctx, int direction, const float* xyz, const floa
   const unsigned grid = (unsigned)((n_tracks + T - 1) / T);
   ctx->tick(tid, st);
   if (direction > 0)
-    k_fit<float><<<grid, T, 0, st>>>(ctx->geom_dev.as<GeomDev>(), xyz, lcov, layer, n_hits, hits, K, init_par,
+    k_fit<<<grid, T, 0, st>>>(ctx->geom_dev.as<GeomDev>(), xyz, lcov, layer, n_hits, hits, K, init_par,
                                      init_cov, n_tracks, align, x0, out_par, out_cov, out_chi2, out_ok, ckpt);
   else
     k_fit_inward<<<grid, T, 0, st>>>(ctx->geom_dev.as<GeomDev>(), xyz, lcov, layer, n_hits, hits, K, init_par,

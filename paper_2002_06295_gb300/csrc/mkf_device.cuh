@@ -295,9 +295,11 @@ struct PosState {
 };
 
 // Predicted chi2 (2 dof) of a hit against a propagated state; returns +inf
-// when the state is not in the hit's half plane.  Values at or above `cut`
-// are only guaranteed to be >= cut (the bound below is applied to the values
-// that would be accepted).
+// when the state is not in the hit's half plane, and also for every hit that
+// is not below `cut`: chi2 = num/det < cut is decided as num < cut det
+// without a division (det > 0), so the divisions run only for accepted hits
+// and use the fast reciprocal (2 ulp; chi2 values feed scores whose ties are
+// resolved at 1e-4 relative, far above that).
 __device__ __forceinline__ float hit_chi2(int kind, const PosState& q, const HitRec& h, float cut) {
   if (!(fmaf(h.c, q.x, h.s * q.y) > 0.0f)) return INFINITY;
   float ra = fmaf(h.s, q.x, -h.c * q.y);
@@ -315,14 +317,15 @@ __device__ __forceinline__ float hit_chi2(int kind, const PosState& q, const Hit
   float Raa = haa + h.v00, Rab = hab + h.v01, Rbb = hbb + h.v11;
   float det = fmaf(Raa, Rbb, -Rab * Rab);
   float num = fmaf(Rbb * ra, ra, fmaf(-2.0f * Rab * ra, rb, Raa * rb * rb));
+  if (!(det > 0.0f) || !(num < cut * det)) return INFINITY;
   // For positive-definite R, chi2 >= r_a^2/R_aa and chi2 >= r_b^2/R_bb exactly
   // (Cauchy-Schwarz); when R is so ill-conditioned that FP32 rounding breaks
   // those bounds (elongated position uncertainty seen from a rotated hit
   // frame), the bound is the trustworthy value.  It keeps every accepted hit
-  // inside the search window, which is built on the same bound.
-  float chi2 = det > 0.0f ? num / det : INFINITY;
-  if (chi2 < cut) chi2 = fmaxf(chi2, fmaxf(ra * ra / Raa, rb * rb / Rbb));
-  return chi2;
+  // inside the search window, which is built on the same bound with a 5 %
+  // margin (far above the reciprocal's 2 ulp).
+  const float chi2 = __fdividef(num, det);
+  return fmaxf(chi2, fmaxf(__fdividef(ra * ra, Raa), __fdividef(rb * rb, Rbb)));
 }
 
 // Box test ahead of the chi2: the residuals of hit_chi2 against the

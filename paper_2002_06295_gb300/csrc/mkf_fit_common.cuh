@@ -1,8 +1,10 @@
-// mkf_fit_common.cuh -- pieces shared by the fit and its adjoint: a listed
-// hit in its aligned local frame, and one outward/inward step onto its surface.
+// mkf_fit_common.cuh -- pieces shared by the fits, the overlap search and the
+// fit adjoint: a listed hit in its aligned local frame, and one outward or
+// inward step onto its surface with the covariance in U-D form.
 #pragma once
 #include "mkf_device.cuh"
 #include "mkf_internal.h"
+#include "mkf_ud.cuh"
 
 namespace mkf {
 
@@ -50,47 +52,32 @@ __device__ __forceinline__ bool load_fit_hit(const GeomDev* __restrict__ g, cons
   return true;
 }
 
-// Multiple scattering added to the transported covariance.  The term only adds
-// to two diagonal entries, so its FP32 value (relative error ~1e-7) is as good
-// as an FP64 one for an FP64 covariance, at a fraction of the FP64 work.
-__device__ __forceinline__ void add_material_step(int kind, float x0, float x, float y, float cphi, float sphi,
-                                                  float kappa, float sin_t, float cos_t, float C[21]) {
-  add_material(kind, x0, x, y, cphi, sphi, kappa, sin_t, cos_t, C);
-}
-__device__ __forceinline__ void add_material_step(int kind, double x0, double x, double y, double cphi, double sphi,
-                                                  double kappa, double sin_t, double cos_t, double C[21]) {
-  if (!(x0 > 0.0)) return;
-  const float st = float(sin_t);
-  const float th2 = highland_theta0_sq(kind, float(x0), float(x), float(y), float(cphi), float(sphi), float(kappa), st,
-                                       float(cos_t));
-  C[ci(4, 4)] += double(th2) / (sin_t * sin_t);
-  C[ci(5, 5)] += double(th2);
-}
-
-// Propagate (p, C) onto the hit's surface in direction dir and add its
-// material.  Returns false when the surface is not reached.
-template <class T> __device__ __forceinline__ bool step_to(const FitHit<T>& f, T p[6], T C[21], T ck, int dir) {
-  T sin_t, cos_t;
+// Propagate the state onto the hit's surface in direction dir, transporting
+// the U-D factors of its covariance and adding the surface's multiple
+// scattering (Highland, on phi and theta).  Returns false when the surface is
+// not reached.
+__device__ __forceinline__ bool step_to_ud(const FitHit<float>& f, float p[6], UD6& u, float ck, int dir) {
+  float sin_t, cos_t;
   msincos(p[5], &sin_t, &cos_t);
-  const T cot_t = cos_t / sin_t;
-  const T omega = ck * p[3];
-  T sph, cph;
+  const float cot_t = cos_t / sin_t;
+  const float omega = ck * p[3];
+  float sph, cph;
   msincos(p[4], &sph, &cph);
-  T s;
-  if (f.kind == 0) {
-    s = cylinder_path(p[0], p[1], cph, sph, omega, f.pos, dir);
-  } else {
-    s = plane_path(p[2], cot_t, f.pos, dir);
-  }
-  if (!(mabs(vv(s)) < INFINITY)) return false;
+  const float s = f.kind == 0 ? cylinder_path(p[0], p[1], cph, sph, omega, f.pos, dir)
+                              : plane_path(p[2], cot_t, f.pos, dir);
+  if (!(fabsf(s) < INFINITY)) return false;
   const auto h = helix_at(p[0], p[1], p[2], p[4], cph, sph, cot_t, omega, s);
   const auto J = transport_jacobian(f.kind, p, h, s, omega, ck, cot_t, sin_t);
-  similarity(J, C);
+  float q_phi = 0.0f, q_theta = 0.0f;
+  if (f.x0 > 0.0f) {
+    q_theta = highland_theta0_sq(f.kind, f.x0, h.x, h.y, h.cphi, h.sphi, p[3], sin_t, cos_t);
+    q_phi = q_theta / (sin_t * sin_t);
+  }
+  ud_transport(J, u, q_phi, q_theta);
   p[0] = h.x;
   p[1] = h.y;
   p[2] = h.z;
   p[4] = wrap_phi(h.phi);
-  add_material_step(f.kind, f.x0, h.x, h.y, h.cphi, h.sphi, p[3], sin_t, cos_t, C);
   return true;
 }
 

@@ -1,7 +1,8 @@
 // overlaps.cu -- recovery of hits in overlapping detector modules (Sec. 3:
 // more than one hit per layer assigned to a track).  The paper plans the
 // feature without fixing a rule; the reading here: run the forward fit of
-// each track (the fit's own steps: propagate, material, update); after the
+// each track (the fit's own steps: propagate, material, update, with the
+// covariance in U-D form); after the
 // update with its hit h on layer l, the overlap hit is the other binned hit of
 // that layer and event, inside the adjacent-module box around h (|R sin(phi_2
 // - phi_h)| <= max_drphi with cos > 0, R the layer radius on a barrel or h's
@@ -78,16 +79,20 @@ __device__ __forceinline__ void track_overlaps(const GeomDev* __restrict__ g, co
   for (int i = 0; i < 6; ++i) p[i] = init_par[i * NT + t];
 #pragma unroll
   for (int i = 0; i < 21; ++i) C[i] = init_cov[i * NT + t];
+  UD6 u;
+  ud_from_cov(C, u);
   for (int k = 0; k < K; ++k) {
     FitHit<float> f;
     const int h = row[k];
     if (!load_fit_hit(g, xyz, lcov, layer, H, h, (const float*)nullptr, (const float*)nullptr, f)) continue;
-    if (!step_to(f, p, C, ck, +1)) break;
-    kf_update(f.kind, p, C, f.m);
+    if (!step_to_ud(f, p, u, ck, +1)) break;
+    ud_update(f.kind, p, u, f.m);
     ++n_fit;
     // search window around the updated state on the same layer
     const LayerDev ly = g->L[f.layer];
-    const PosState q{p[0], p[1], p[2], C[ci(0, 0)], C[ci(1, 0)], C[ci(1, 1)], C[ci(2, 0)], C[ci(2, 1)], C[ci(2, 2)]};
+    float cp[6];
+    ud_pos_block(u, cp);
+    const PosState q{p[0], p[1], p[2], cp[0], cp[1], cp[2], cp[3], cp[4], cp[5]};
     const float r = sqrtf(fmaf(q.x, q.x, q.y * q.y));
     if (!(r > 0.f)) continue;
     const float c = q.x / r, s = q.y / r;

@@ -158,10 +158,8 @@ def compare(gpu, ref, sel=None, fragile_tol=FRAGILE_TOL):
 
 
 def cov_ok(ce, frac=0.99, tol=COV_RTOL, cap=1e-3):
-    """Covariance agreement for an FP32 path: at least `frac` of the tracks
-    within `tol` (scale metric) and none beyond `cap`.  A covariance stored in
-    FP32 keeps about 6e-8 / (1 - rho^2) of relative information on a pair of
-    parameters with correlation rho; pixel hits drive (z, theta) and
-    (r, theta) correlations to 1 - rho^2 ~ 2e-4, hence the cap."""
+    """Covariance agreement where a stated fraction of the results may exceed
+    the bar: at least `frac` of the tracks within `tol` (scale metric) and
+    none beyond `cap`."""
     per = ce.max(1) if ce.ndim == 2 else ce
     return bool((per < tol).mean() >= frac and per.max() < cap)

@@ -1,8 +1,21 @@
 """The hand-written adjoint of the Kalman fit (through the C ABI and through
 torch.autograd) against the oracle's dual-number gradient and FP64 central
-finite differences (h = 1e-6): within 1e-3 relative, per gradient group
-(hit x, y, z; alignment dr, dphi, dz; thickness) both norm-wise and for each
-component measured against the group's largest component."""
+finite differences (h = 1e-6).
+
+Each gradient component g is compared with its FP64 value r on its own:
+|g - r| <= 1e-3 |r| + f, where f is the error that FP32 positions alone put
+into a component.  A residual is a difference of positions of up to R_max
+(~100 cm) that carry FP32 rounding, so it is off by up to ~4 eps R_max
+(eps = 2^-24, the hit and the propagated state each rounded about twice), and
+d chi2 / d x = 2 r / sigma^2 inherits 2 (4 eps R_max) / sigma_min^2: the
+hit-gradient floor f_hit = 8 eps R_max / sigma_min^2 (0.5 /cm for 100 um hits
+at 100 cm).  A layer's alignment or thickness gradient is a sum of the
+tracks' terms T_t, often with strong cancellation; each term carries FP32
+error of ~1e-5 of itself, so the sum's floor is 1e-4 sum_t |T_t| (the terms
+come from the oracle, one track at a time), and no less than f_hit sqrt(n)
+for n tracks (times the layer radius for the azimuthal shift, whose lever
+arm it is).  Above the floor the bar is 1e-3 relative, per component; the
+norm-wise error of each group is also held to 1e-3."""
 import numpy as np
 import pytest
 import torch
@@ -38,13 +51,40 @@ def _inputs(n=300, seed=21, geom=None, pt=(1.0, 10.0), eta=0.8):
     return g, ev, hits, q(sp), q(sc), align, x0, up
 
 
-def _group_errors(got, ref):
-    """(largest error relative to the group's largest component, norm-wise
-    relative error).  Small components of a layer gradient are sums over many
-    tracks with strong cancellation, so their own relative error reflects the
-    FP32 noise of the large terms; the group's scale is the fair yardstick."""
+EPS32 = 2.0 ** -24
+
+
+def _floors(g, ev, hits, sp, sc, up, align, x0):
+    """FP32 floors of the gradient components (module docstring): hits,
+    per-layer (dr, dphi, dz) [L, 3] and thickness [L]."""
+    import oracle
+    used = hits[hits >= 0]
+    r_max = float(np.abs(g.table()[:, 1:4]).max())
+    var_min = float(ev.hit_lcov[used][:, :2].min())
+    f_hit = 8 * EPS32 * r_max / var_min
+    n = np.bincount(ev.hit_layer[used], minlength=g.n_layers).astype(np.float64)
+    radius = np.where(np.asarray(g.kind) == 0, np.abs(g.table()[:, 1]), np.abs(g.table()[:, 3]))
+    f_layer = np.stack([f_hit * np.sqrt(n), f_hit * np.sqrt(n) * radius, f_hit * np.sqrt(n)], 1)
+    # sum over tracks of |each track's term|, from the oracle track by track
+    geo = oracle.Geo.of(g)
+    abs_a, abs_x = np.zeros((g.n_layers, 3)), np.zeros(g.n_layers)
+    for t in range(hits.shape[0]):
+        pick = lambda k: None if up.get(k) is None else up[k][t:t + 1]
+        _, ga, gx = oracle.fit_grad(geo, ev.hit_xyz, ev.hit_lcov, ev.hit_layer, hits[t:t + 1], sp[t:t + 1],
+                                    sc[t:t + 1], up["g_chi2"][t:t + 1], g_par=pick("g_par"), g_cov=pick("g_cov"),
+                                    align=align, x0=x0)
+        abs_a += np.abs(ga)
+        abs_x += np.abs(gx)
+    return f_hit, np.maximum(f_layer, 1e-4 * abs_a), 1e-4 * abs_x
+
+
+def _component_errors(got, ref, floor):
+    """(largest |g - r| / (1e-3 |r| + floor) over the components, norm-wise
+    relative error of the group).  The first must not exceed 1."""
     err = np.abs(got - ref)
-    return float(err.max() / np.abs(ref).max()), float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    bound = GRAD_RTOL * np.abs(ref) + floor
+    ratio = np.where(err > 0, err / np.where(bound > 0, bound, 1e-300), 0.0)
+    return float(ratio.max()), float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
 
 
 @pytest.mark.parametrize("upstream", ["chi2", "all"])
@@ -70,15 +110,17 @@ def test_adjoint_matches_oracle_gradient(upstream):
     rh, ra, rx = oracle.fit_grad(oracle.Geo.of(g), ev.hit_xyz, ev.hit_lcov, ev.hit_layer, hits, sp, sc, up["g_chi2"],
                                  g_par=up["g_par"], g_cov=up["g_cov"], align=align, x0=x0)
     used = np.unique(hits[hits >= 0])
+    f_hit, f_layer, f_x0 = _floors(g, ev, hits, sp, sc, up, align, x0)
     report = {}
-    for name, a, b in (("hit_x", gh[used, 0], rh[used, 0]), ("hit_y", gh[used, 1], rh[used, 1]),
-                       ("hit_z", gh[used, 2], rh[used, 2]), ("align_dr", ga[:, 0], ra[:, 0]),
-                       ("align_dphi", ga[:, 1], ra[:, 1]), ("align_dz", ga[:, 2], ra[:, 2]), ("x0", gx, rx)):
-        report[name] = _group_errors(a, b)
-    print("adjoint vs oracle (max elementwise, norm-wise):", report)
-    for name, (emax, enorm) in report.items():
+    for name, a, b, f in (("hit_x", gh[used, 0], rh[used, 0], f_hit), ("hit_y", gh[used, 1], rh[used, 1], f_hit),
+                          ("hit_z", gh[used, 2], rh[used, 2], f_hit), ("align_dr", ga[:, 0], ra[:, 0], f_layer[:, 0]),
+                          ("align_dphi", ga[:, 1], ra[:, 1], f_layer[:, 1]),
+                          ("align_dz", ga[:, 2], ra[:, 2], f_layer[:, 2]), ("x0", gx, rx, f_x0)):
+        report[name] = _component_errors(a, b, f)
+    print("adjoint vs oracle (worst component / its bound, norm-wise):", report)
+    for name, (worst, enorm) in report.items():
         assert enorm < GRAD_RTOL, (name, report)
-        assert emax < GRAD_RTOL, (name, report)
+        assert worst <= 1.0, (name, report)
     ctx.close()
 
 
@@ -138,20 +180,28 @@ def test_adjoint_matches_central_differences():
         return float(up["g_chi2"] @ chi2)
 
     h = 1e-6
+    f_hit, f_layer, f_x0 = _floors(g, ev, hits, sp, sc, dict(g_chi2=up["g_chi2"]), align, x0)
     rng = np.random.default_rng(5)
     for hid in rng.choice(np.unique(hits[hits >= 0]), 8, replace=False):
         for c in range(3):
             a = ev.hit_xyz.copy(); b = a.copy(); a[hid, c] += h; b[hid, c] -= h
             fd = (loss(hx=a) - loss(hx=b)) / (2 * h)
-            assert abs(gh[hid, c] - fd) <= GRAD_RTOL * np.abs(gh[:, c]).max(), (hid, c, gh[hid, c], fd)
+            assert abs(gh[hid, c] - fd) <= GRAD_RTOL * abs(fd) + f_hit, (hid, c, gh[hid, c], fd)
     for l in (0, 6, 13):
         for c in range(3):
             a = align.copy(); b = align.copy(); a[l, c] += h; b[l, c] -= h
             fd = (loss(al=a) - loss(al=b)) / (2 * h)
-            assert abs(ga[l, c] - fd) <= GRAD_RTOL * np.abs(ga[:, c]).max(), (l, c, ga[l, c], fd)
-        a = x0.copy(); b = x0.copy(); a[l] += h; b[l] -= h
-        fd = (loss(xx=a) - loss(xx=b)) / (2 * h)
-        assert abs(gx[l] - fd) <= GRAD_RTOL * np.abs(gx).max(), (l, gx[l], fd)
+            assert abs(ga[l, c] - fd) <= GRAD_RTOL * abs(fd) + f_layer[l, c], (l, c, ga[l, c], fd)
+        # thickness: x/X0 ~ 0.01 enters through the scattering variance only,
+        # so its central difference takes a 1e-4 step (five-point stencil)
+        hx = 1e-4
+
+        def at(k):
+            a = x0.copy()
+            a[l] += k * hx
+            return loss(xx=a)
+        fd = (-at(2) + 8 * at(1) - 8 * at(-1) + at(-2)) / (12 * hx)
+        assert abs(gx[l] - fd) <= GRAD_RTOL * abs(fd) + f_x0[l], (l, gx[l], fd, f_x0[l])
     ctx.close()
 
 
@@ -217,9 +267,11 @@ def test_fit_gradient_full_size_sampled_tracks():
     geo = oracle.Geo.of(g)
     rh, _, _ = oracle.fit_grad(geo, ev.hit_xyz, ev.hit_lcov, ev.hit_layer, hits[sel], sp[sel], sc[sel], np.ones(sel.size))
     _, _, rchi2, _ = oracle.fit(geo, ev.hit_xyz, ev.hit_lcov, ev.hit_layer, hits[sel], sp[sel], sc[sel])
-    assert np.abs(chi2[sel] - rchi2).max() <= 1e-3 * np.maximum(rchi2, 1.0).max()
+    # each sampled track's chi2 on its own
+    assert np.all(np.abs(chi2[sel] - rchi2) <= 1e-3 * rchi2), np.max(np.abs(chi2[sel] - rchi2) / rchi2)
     used = hits[sel].ravel()
+    f_hit = 8 * EPS32 * float(np.abs(g.table()[:, 1:4]).max()) / float(ev.hit_lcov[used][:, :2].min())
     for c in range(3):
-        emax, enorm = _group_errors(gh[used, c], rh[used, c])
-        assert enorm < GRAD_RTOL and emax < GRAD_RTOL, (c, emax, enorm)
+        worst, enorm = _component_errors(gh[used, c], rh[used, c], f_hit)
+        assert enorm < GRAD_RTOL and worst <= 1.0, (c, worst, enorm)
     ctx.close()

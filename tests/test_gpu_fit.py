@@ -1,6 +1,6 @@
 """Parity of the CUDA fixed-assignment Kalman fit (outward and inward) with the
 FP64 oracle: parameters within 1e-4 relative, covariances within 1e-4 of
-sqrt(C_ii C_jj), chi2 within 1e-4 relative (plus 1e-3 absolute)."""
+sqrt(C_ii C_jj), chi2 within 1e-3 relative."""
 import numpy as np
 import pytest
 import torch
@@ -51,7 +51,7 @@ def test_forward_fit_matches_oracle(with_align):
     print("forward fit: par err per parameter", pe.max(0), "cov err", ce.max(),
           "chi2 rel err", (np.abs(gx - chi2) / chi2).max())
     assert pe.max() < PAR_RTOL
-    assert cov_ok(ce)
+    assert ce.max() < COV_RTOL
     assert (np.abs(gx - chi2) <= CHI2_RTOL * chi2).all()
     # checkpoint 0 is the initial state
     ck = ckpt.cpu().numpy()
@@ -109,7 +109,9 @@ def test_fit_cmslike_mixed_surfaces():
     assert pe.max() < PAR_RTOL
     ce = cov_rel_err(gc[good], cov[good])
     print("cms-like fit: cov err max", ce.max(), "fraction within 1e-4", (ce.max(1) < COV_RTOL).mean())
-    assert cov_ok(ce, frac=0.9, cap=2e-3)
+    # the U-D factorised FP32 covariance keeps the small conditional variances
+    # of pixel hits and strip disks: every track within 1e-4
+    assert ce.max() < COV_RTOL
     ctx.close()
 
 
@@ -147,7 +149,7 @@ def test_backward_fit_cmslike_mixed_surfaces():
     print("cms-like backward fit: par err per parameter", pe.max(0), "cov err max", ce.max(),
           "fraction within 1e-4", (ce.max(1) < COV_RTOL).mean())
     assert pe.max() < PAR_RTOL
-    assert cov_ok(ce, frac=0.9, cap=2e-3)
+    assert ce.max() < COV_RTOL
     ctx.close()
 
 
@@ -186,7 +188,10 @@ def test_backward_fit_built_c2_tracks():
     print("built C2 backward fit: %d tracks, par err per parameter" % good.sum(), pe.max(0), "cov err max",
           ce.max(), "fraction within 1e-4", (ce.max(1) < COV_RTOL).mean())
     assert pe.max() < PAR_RTOL
-    assert cov_ok(ce, frac=0.9, cap=2e-3)
+    # both sides FP64: the kernel updates in the plain gain form, the oracle in
+    # the Joseph form; on built tracks whose wrong picks leave the fit
+    # ill-conditioned the two roundings part by up to 1.6e-4 (2 of ~3800)
+    assert cov_ok(ce, frac=0.999, cap=2e-4)
     ctx.close()
 
 

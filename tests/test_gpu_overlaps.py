@@ -1,14 +1,22 @@
 """Overlap-hit recovery on the GPU (Sec. 3, hits in overlapping modules)
 against the FP64 oracle, on a CMS-like event whose barrel crossings leave a
-second hit 30 % of the time.  The FP32 fit states give chi2 values within ~1 %
-of the oracle's (residuals of tens of microns from positions rounded to
-~0.1 micron), so the selection is compared where the oracle's choice is
-clear: its best chi2 more than 2 % away from the cut and more than 2 % below
-the runner-up (or, for "none", its best more than 2 % above the cut); there
-the hit must be the same and the chi2 within 2 %.  The comparison covers the
-tracks whose FP64 fit is sound (more than 95 % of them).  Also: tracks built
-on the GPU recover the simulation's overlap hits, and the work counters add
-up."""
+second hit 30 % of the time; both sides see the same float32 inputs.
+
+An overlap hit's chi2 is formed from residuals of tens of microns between
+positions of up to R_max ~ 110 cm that carry FP32 rounding, ~4 eps R_max
+(eps = 2^-24) each, so the FP32 chi2 of a residual r/sigma carries
+2 sqrt(chi2) d + d^2 with d = 4 eps R_max / sigma_min on top of its 1e-3
+relative bar.  A slot's choice is compared exactly where the oracle's choice
+is clear of that: its best chi2 more than 1e-3 (plus that error) away from the
+cut and below the runner-up.
+
+Every track is compared.  The tracks whose fit fails (chi2/ndf > 5: central
+loopers that reach the disks only after several turns, and forward tracks
+whose seed theta is off by a large fraction of theta, where one linearised
+pass cannot follow the helix) have states that FP32 and FP64 carry apart; on
+them at most 0.5 % of the clear slots may differ, and every other track must
+agree on every clear slot.  Also: tracks built on the GPU recover the
+simulation's overlap hits, and the work counters add up."""
 import numpy as np
 import pytest
 import torch
@@ -25,9 +33,16 @@ def _built():
     __graft_entry__.build()
 
 
+EPS32 = 2.0 ** -24
+
+
 @pytest.fixture(scope="module")
 def event():
-    return sev.make_config_event(2, overlap_frac=0.3)
+    ev = sev.make_config_event(2, overlap_frac=0.3)
+    q = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    ev.hit_xyz, ev.hit_lcov = q(ev.hit_xyz), q(ev.hit_lcov)
+    ev.seed_par, ev.seed_cov = q(ev.seed_par), q(ev.seed_cov)
+    return ev
 
 
 def _setup(ev):
@@ -56,20 +71,23 @@ def test_true_tracks_equal_oracle(event):
                           ev.seed_cov[sel], chi2_cut=CUT)
     slots = hits >= 0
     best = ref["best"]
-    # tracks whose oracle fit is sound: mean chi2 per measurement below 5 and
-    # no negative chi2 (on ill-conditioned strip disks the FP64 plain-form
-    # covariance of a track that fits badly can lose positive definiteness)
+    assert not (best < 0).any()   # the Joseph-form oracle keeps every R positive
+    r_max = float(np.abs(ev.geom.table()[:, 1:4]).max())
+    d = 4 * EPS32 * r_max / np.sqrt(ev.hit_lcov[:, :2].min())
+    chi2_err = lambda c: 1e-3 * c + 2 * np.sqrt(np.maximum(c, 0)) * d + d * d
+    # clear: no candidate near the cut, or a clear winner below it
+    clear = slots & ((best > CUT + chi2_err(CUT)) | ((best < CUT - chi2_err(CUT)) & (ref["gap"] * best > 2 * chi2_err(best))))
+    assert clear.sum() > 0.99 * slots.sum()
     _, _, fchi2, fok = oracle.fit(oracle.Geo.of(ev.geom), ev.hit_xyz, ev.hit_lcov, ev.hit_layer, hits,
                                   ev.seed_par[sel], ev.seed_cov[sel])
-    healthy = (fok == 1) & (fchi2 < 5.0 * 2 * slots.sum(1)) & ~(best < 0).any(1)
-    assert healthy.mean() > 0.95
-    # clear: no candidate near the cut, or a clear winner well below it
-    clear = slots & healthy[:, None] & ((best > 1.02 * CUT) | ((best < 0.98 * CUT) & (ref["gap"] > 0.02)))
-    assert clear.sum() > 0.95 * slots[healthy].sum()
-    assert np.array_equal(gh[clear], ref["hit"][clear])
-    found = clear & (ref["hit"] >= 0)
+    failed = (fok != 1) | (fchi2 > 5.0 * 2 * slots.sum(1))
+    assert failed.mean() < 0.06
+    same = gh == ref["hit"]
+    assert same[clear & ~failed[:, None]].all()
+    assert (~same[clear & failed[:, None]]).sum() <= 0.005 * (clear & failed[:, None]).sum()
+    found = clear & (ref["hit"] >= 0) & same
     assert found.sum() > 1000
-    assert np.allclose(gc[found], ref["chi2"][found], rtol=2e-2, atol=1e-3)
+    assert np.all(np.abs(gc[found] - ref["chi2"][found]) <= chi2_err(ref["chi2"][found]))
     assert np.all(gh[~slots] == -1)
     w = mkf.mkf_get_overlap_stats(ctx)
     assert w["found"] == int((gh >= 0).sum()) and w["hits_fitted"] <= int(slots.sum())
