@@ -601,11 +601,34 @@ def measured_peaks():
         return {}
 
 
-def workload_events(synth, cfg_id, rank=0):
-    """The events of one timed step of a workload (rank r takes its own events)."""
-    if synth.WORKLOAD_SPECS[cfg_id]["n_events"] == 1:
-        return [synth.make_config_event(cfg_id, rank)]
-    return [synth.make_config_event(cfg_id, rank * 10000 + e) for e in range(synth.WORKLOAD_SPECS[cfg_id]["n_events"])]
+def shard_range(n_total, rank, world):
+    """Contiguous range [start, end) of events 0..n_total-1 for one rank: the
+    first n_total % world ranks take one event more.  Events are independent
+    (Sec. 2: events are processed in parallel), so the ranks need no exchange
+    while they build."""
+    base, extra = divmod(n_total, world)
+    start = rank * base + min(rank, extra)
+    return start, start + base + (1 if rank < extra else 0)
+
+
+def workload_events(synth, cfg_id, rank=0, world=1):
+    """The events of one timed step of a workload on one rank.  Weak scaling:
+    the global event sequence of a step holds world x n_events events (a
+    workload's n_events per rank) and each rank takes its contiguous range."""
+    n = synth.WORKLOAD_SPECS[cfg_id]["n_events"]
+    start, end = shard_range(n * world, rank, world)
+    return [synth.make_config_event(cfg_id, e) for e in range(start, end)]
+
+
+def gather_results(dist, local):
+    """Rank 0 receives every rank's results in rank order (a host-side gather of
+    the ranks' tracks, the only exchange event sharding needs); other ranks
+    get None.  The identity on one rank."""
+    if not dist:
+        return [local]
+    out = [None] * dist.get_world_size() if dist.get_rank() == 0 else None
+    dist.gather_object(local, out, dst=0)
+    return out
 
 
 def time_path(mkf, dev, evs, spec, steps, warmup, dist=None, clocks=None, graph=True):
@@ -882,7 +905,7 @@ def main():
 
     dev = torch.device("cuda", local)
     cfg_id = {"c2": 2, "c3": 3, "c5": 5}[args.workload]
-    evs = workload_events(synth, cfg_id, rank)
+    evs = workload_events(synth, cfg_id, rank, world)
     clocks = ClockSampler(local)
     r = time_path(mkf, dev, evs, synth.WORKLOAD_SPECS[cfg_id], args.steps, args.warmup, dist=dist, clocks=clocks,
                   graph=not args.no_graph)

@@ -33,6 +33,45 @@ def rand_cov(rng, scale=(0.1, 0.1, 0.1, 0.02, 0.05, 0.05)):
     return oracle.pack_cov(M)
 
 
+# --- multiple scattering: the Highland width at hand-computed points --------
+
+# theta0 = 0.0136 GeV / (beta p) sqrt(t) (1 + 0.038 ln t), pion mass 0.13957
+# GeV, t = x/X0 / |cos(incidence)|; worked out by hand (to 12 digits) for:
+#  A: p = 1 GeV, radial track through a barrel layer at normal incidence,
+#     x/X0 = 0.01: beta = 0.990400134552, theta0 = 1.13288030327e-3;
+#  B: p = 0.2 GeV, theta = pi/3 through a disk, x/X0 = 0.04, t = 0.08:
+#     beta = 0.820059380940, theta0 = 2.12025333159e-2;
+#  C: p = 3 GeV, theta = pi/4, radial in phi through a barrel layer,
+#     x/X0 = 0.02, t = 0.02 / sin(pi/4) = 0.0282842712475:
+#     beta = 0.998919543334, theta0 = 6.59828590496e-4.
+# C_thetatheta grows by theta0^2 and C_phiphi by theta0^2 / sin^2(theta).
+HIGHLAND_CASES = [
+    # kind, pos, lo, hi, x0, (kappa, phi, theta), theta0^2, theta0^2 / sin^2 theta
+    (0, 10.0, -50.0, 50.0, 0.01, (1.0, 0.0, np.pi / 2), 1.28341778153e-6, 1.28341778153e-6),
+    (1, 20.0, 1.0, 100.0, 0.04, (5.77350269189626, 0.3, np.pi / 3), 4.49547419013e-4, 5.99396558684e-4),
+    (0, 10.0, -50.0, 50.0, 0.02, (0.471404520791032, 0.0, np.pi / 4), 4.35373768836e-7, 8.70747537672e-7),
+]
+
+
+@pytest.mark.parametrize("case", range(len(HIGHLAND_CASES)))
+def test_highland_width_at_hand_computed_points(orc, case):
+    """With B = 0 the direction at the crossing is the start direction, so the
+    material term the oracle adds at the layer is the Highland width of the
+    hand-computed cases above, on C_thetatheta and (divided by sin^2 theta) on
+    C_phiphi, and nothing else changes."""
+    kind, pos, lo, hi, x0, (kappa, phi, theta), th2, phiphi = HIGHLAND_CASES[case]
+    geo = orc.Geo(np.array([[kind, pos, lo, hi, x0]]), 0.0)
+    p = np.array([0.0, 0.0, 0.0, kappa, phi, theta])
+    C = orc.pack_cov(np.diag([1e-4, 1e-4, 1e-4, 1e-4, 1e-4, 1e-4]))
+    _, c_mat, _ = orc.transport(geo, p, C, 0, +1, material=True)
+    _, c_none, _ = orc.transport(geo, p, C, 0, +1, material=False)
+    d = c_mat - c_none
+    assert abs(d[orc.cov_index(5, 5)] - th2) <= 1e-10 * th2
+    assert abs(d[orc.cov_index(4, 4)] - phiphi) <= 1e-10 * phiphi
+    others = [k for k in range(21) if k not in (orc.cov_index(4, 4), orc.cov_index(5, 5))]
+    assert np.all(d[others] == 0.0)
+
+
 # --- helix closed forms ------------------------------------------------------
 
 def test_helix_closure(orc):
