@@ -159,14 +159,18 @@ mkf_status mkf_cluster_strips(mkf_ctx* ctx, const uint16_t* adc, const uint16_t*
  *    layer-1 and layer-3 hits and the line through the layer-0 and layer-3
  *    hits, with a fixed diagonal covariance (sigma x, y 0.01 cm, z 0.05 cm,
  *    kappa 5 % + 0.01 /GeV, phi and theta 5 mrad).
- * Decisions are taken in FP32.  The call synchronises `stream` once (it reads
- * back the number of hit pairs to size its working memory), so it cannot be
- * captured in a CUDA graph.  Outputs (DEVICE, caller-owned):
+ * Decisions are taken in FP32.  By default the call synchronises `stream` once
+ * (it reads back the number of hit triplets to size its working memory), so
+ * it cannot be captured in a CUDA graph; with a fixed triplet capacity set by
+ * mkf_set_seed_config it does not synchronise and can be captured.  Outputs
+ * (DEVICE, caller-owned):
  *   ev_seed_off [n_events + 1] int64: seeds of event e are [off[e], off[e+1]);
  *     n = ev_seed_off[n_events] is the number found;
  *   seed_par [6][n], seed_cov [21][n] float: laid out with column stride n
- *     (so the first 6 n and 21 n floats are ready for mkf_build_tracks);
- *     buffers hold max_seeds columns;
+ *     (so the first 6 n and 21 n floats are ready for mkf_build_tracks), or
+ *     with column stride max_seeds under a fixed triplet capacity (so that
+ *     mkf_build_tracks can be called with n_seeds = max_seeds before n is known
+ *     on the host; see there); buffers hold max_seeds columns;
  *   seed_hits [n][4] int: caller hit ids on layers 0..3.
  * If n > max_seeds nothing but ev_seed_off is written and mkf_sync returns
  * MKF_ERR_CAPACITY.  The seeds are in a fixed order (event, then layer-0 hit
@@ -176,6 +180,15 @@ mkf_status mkf_cluster_strips(mkf_ctx* ctx, const uint16_t* adc, const uint16_t*
  * reach 1.1 times the layer-3 radius, or rphi_tol >= R2 / 2. */
 mkf_status mkf_seed_tracks(mkf_ctx* ctx, float pt_min, float z_max, float rphi_tol, float z_tol, int64_t max_seeds,
                            float* seed_par, float* seed_cov, int* seed_hits, int64_t* ev_seed_off, void* stream);
+
+/* Fixed triplet capacity of mkf_seed_tracks.  max_triplets = 0 (default):
+ * the triplet list is sized from its count, read back once per call (the call
+ * synchronises its stream).  max_triplets > 0: the list holds that many
+ * triplets, nothing is read back, and the call can be captured in a CUDA
+ * graph; a list that does not fit is not searched, ev_seed_off then counts no
+ * seeds of the events past the fit, and mkf_sync returns MKF_ERR_CAPACITY.
+ * The paper has no counterpart.  MKF_ERR_ARG outside 0..2^31-2. */
+mkf_status mkf_set_seed_config(mkf_ctx* ctx, int64_t max_triplets);
 
 /* Work counters of the last mkf_seed_tracks (synchronises `stream`): [0]
  * layer-1 hits examined in the pair windows, [1] pairs that passed, [2]
@@ -235,7 +248,14 @@ mkf_status mkf_get_binning(mkf_ctx* ctx, int* perm, int* bin_off, int64_t* n_bin
  * (drop a track sharing more than dup_frac of min(n_a, n_b) hits with a
  * better-scoring kept track).
  *   seed_par [6][S], seed_cov [21][S]   seed states
- *   ev_seed_off [E+1]                    int64 CSR offsets of each event's seeds
+ *   ev_seed_off [E+1]                    int64 CSR offsets of each event's seeds;
+ *                                        when ev_seed_off[E] (read on the device)
+ *                                        is below S, only those seeds are built
+ *                                        and rows ev_seed_off[E]..S-1 are written
+ *                                        as empty tracks (no hits, zero state,
+ *                                        MKF_TRK_SHORT): hit-based seeds with a
+ *                                        fixed triplet capacity build with
+ *                                        S = max_seeds and no host read-back
  *   max_cands 1..MKF_MAX_CANDS, max_holes >= 0, min_hits >= 0, 0 <= dup_frac <= 1
  * Outputs ([S] arrays, DEVICE; out_layers, out_counts may be NULL):
  *   out_hits [S][L]     hit id at the k-th crossed surface, -1 for a hole or past the end
@@ -358,8 +378,9 @@ mkf_status mkf_fit_tracks(mkf_ctx* ctx, const float* xyz, const float* lcov, con
  * mkf_fit_tracks (init_cov is ignored; ckpt unsupported, pass NULL).
  * Arithmetic: FP64 (the multiple-scattering term in FP32); outputs rounded
  * to FP32.  The prior makes the first updates shrink variances by up to 1e5,
- * and mixed barrel/disk tracks keep correlations close to 1, which neither
- * FP32 nor a 48-bit float pair carries to 1e-4 on every track. */
+ * and on built tracks that carry wrong picks the updates move the state by
+ * hundreds of standard deviations, which an FP32 state (also one with U-D
+ * factorised covariance) does not carry to 1e-4 on every track. */
 mkf_status mkf_fit_backward(mkf_ctx* ctx, const float* xyz, const float* lcov, const int* layer, int64_t n_hits,
                             const int* hits, int K, const float* init_par, int64_t n_tracks, const float* align,
                             const float* x0, float* out_par, float* out_cov, float* out_chi2, int* out_ok,

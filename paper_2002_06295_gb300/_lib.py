@@ -34,6 +34,7 @@ SIGNATURES = {
     "mkf_set_strip_config": (i32, [P, i32, i32, i32]),
     "mkf_seed_tracks": (i32, [P, f32, f32, f32, f32, i64, P, P, P, P, P]),
     "mkf_get_seed_stats": (i32, [P, P, i32, P]),
+    "mkf_set_seed_config": (i32, [P, i64]),
     "mkf_find_overlaps": (i32, [P, P, P, P, i64, P, i32, P, P, i64, f32, f32, f32, P, P, P]),
     "mkf_get_overlap_stats": (i32, [P, P, i32, P]),
     "mkf_cluster_strips": (i32, [P, P, P, P, i32, i32, i32, i32, i32, P, P, P, P, P, i64, P, P]),

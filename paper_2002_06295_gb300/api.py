@@ -231,11 +231,19 @@ def mkf_cluster_strips(ctx, adc, noise_q, bad, max_bad_gap=1, q_min=30, max_out=
     return o
 
 
-def mkf_seed_tracks(ctx, pt_min=0.5, z_max=5.0, rphi_tol=0.05, z_tol=0.1, max_seeds=None, out=None, stream=None):
+def mkf_set_seed_config(ctx, max_triplets=0):
+    ctx._check(ctx.lib.mkf_set_seed_config(ctx.h, int(max_triplets)), "mkf_set_seed_config")
+
+
+def mkf_seed_tracks(ctx, pt_min=0.5, z_max=5.0, rphi_tol=0.05, z_tol=0.1, max_seeds=None, out=None, stream=None,
+                    read_count=True):
     """Hit-based seeding (four innermost barrel layers) from the binned hits.
     Returns dict par [6, n], cov [21, n] (views ready for mkf_build_tracks),
     hits [n, 4], ev_seed_off [E+1] (device int64) and n (read back, one
-    synchronising copy)."""
+    synchronising copy).  With read_count=False (for a fixed triplet capacity,
+    mkf_set_seed_config, e.g. inside a CUDA graph) nothing is read back: n is
+    None and par [6, max_seeds], cov [21, max_seeds], hits [max_seeds, 4] are
+    the whole buffers, in the column stride max_seeds the call then uses."""
     dev = torch.device("cuda", ctx.device)
     cap = int(max_seeds) if max_seeds is not None else max(1024, int(ctx.n_hits))
     E = int(ctx.n_events)
@@ -248,8 +256,14 @@ def mkf_seed_tracks(ctx, pt_min=0.5, z_max=5.0, rphi_tol=0.05, z_tol=0.1, max_se
                                        _ptr(o["par"]), _ptr(o["cov"]), _ptr(o["hits"]),
                                        _ptr(o["ev_seed_off"], torch.int64, "ev_seed_off"), _stream(stream)),
                "mkf_seed_tracks")
-    n = int(o["ev_seed_off"][E].item())
     res = dict(o)
+    if not read_count:
+        res["n"] = None
+        res["par"] = o["par"].view(6, cap)
+        res["cov"] = o["cov"].view(21, cap)
+        res["hits"] = o["hits"].view(cap, 4)
+        return res
+    n = int(o["ev_seed_off"][E].item())
     res["n"] = n
     if n <= cap:
         res["par"] = o["par"][:6 * n].view(6, n)

@@ -84,6 +84,7 @@ struct BuildDev {
   float* out_score;
   float* out_chi2;
   int* out_counts;
+  int* out_flags;
   int* track_nh;
   unsigned long long* seed_ctr;
   unsigned long long* stats;
@@ -243,6 +244,26 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
 
   const float cut = a.chi2_cut;
   const float ck = G.c_kappa;
+  // seeds whose count is known only on the device (hit-based seeding with a
+  // fixed capacity): build the first ev_seed_off[E] of the n_seeds rows and
+  // write the rest as empty tracks
+  int64_t n_run = a.ev_seed_off[a.n_events];
+  n_run = n_run < 0 ? 0 : (n_run < a.n_seeds ? n_run : a.n_seeds);
+  for (int64_t r = n_run + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < a.n_seeds;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t S = a.n_seeds;
+    for (int k = 0; k < 6; ++k) a.out_par[k * S + r] = 0.0f;
+    for (int k = 0; k < 21; ++k) a.out_cov[k * S + r] = 0.0f;
+    a.out_score[r] = 0.0f;
+    a.out_chi2[r] = 0.0f;
+    a.track_nh[r] = 0;
+    if (a.out_counts) a.out_counts[r] = a.out_counts[S + r] = a.out_counts[2 * S + r] = 0;
+    for (int k = 0; k < L; ++k) {
+      a.out_hits[r * L + k] = -1;
+      if (a.out_layers) a.out_layers[r * L + k] = -1;
+    }
+    a.out_flags[r] = MKF_TRK_SHORT;
+  }
   unsigned long long n_steps = 0, n_chi2 = 0, n_full = 0, n_upd = 0, n_nav = 0, n_viol = 0;
 
   // per-group seed state (replicated over the group's lanes)
@@ -263,7 +284,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
     if (want && li == 0) s = atomicAdd(a.seed_ctr, 1ull);
     s = __shfl_sync(0xffffffffu, s, gbase);
     if (!want) return;
-    seed = (int64_t)s < a.n_seeds ? (int64_t)s : -1;
+    seed = (int64_t)s < n_run ? (int64_t)s : -1;
     active = false;
     step = 0;
     if (seed >= 0) {
@@ -872,6 +893,7 @@ cudaError_t launch_build(mkf_ctx* ctx, const BuildArgs& a, cudaStream_t st) {
     d.out_score = a.out_score;
     d.out_chi2 = a.out_chi2;
     d.out_counts = a.out_counts;
+    d.out_flags = a.out_flags;
     d.track_nh = ctx->track_hits.as<int>();
     d.seed_ctr = ctx->seed_ctr.as<unsigned long long>();
     d.stats = ctx->stats.as<unsigned long long>();

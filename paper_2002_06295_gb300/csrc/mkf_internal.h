@@ -88,6 +88,7 @@ struct mkf_ctx {
   mkf::DevBuf seed_stats;                                                       // its work counters
   mkf::DevBuf seed_scratch, seed_loc;   // per-warp triplet lists of the counting pass, their places
   int64_t seed_trip_hint = 0;           // triplets of the last seeding call (sizes the scratch)
+  int64_t seed_trip_cap = 0;            // fixed triplet capacity of seeding (0: sized by a read-back)
   mkf::DevBuf ovl_stats;                                                        // overlap-hit search counters
 
   // optional stage timing (CUDA events on the launch stream)

@@ -222,8 +222,11 @@ __global__ void __launch_bounds__(kSeedThreads)
                     const int* __restrict__ l0_cum, int64_t n_slots, int* __restrict__ tcnt,
                     const int* __restrict__ toff, int4* __restrict__ trip, unsigned long long* __restrict__ stats,
                     int4* __restrict__ scratch, int64_t seg_cap, int64_t* __restrict__ item_loc,
-                    int* __restrict__ overflow) {
+                    int* __restrict__ overflow, int64_t trip_cap = -1) {
   const int lane = threadIdx.x & 31;
+  // write pass launched without a host decision (fixed triplet capacity): it
+  // runs only if a scratch segment overflowed, and only if the list fits
+  if (WRITE && trip_cap >= 0 && (!*(volatile int*)overflow || __ldg(&toff[n_slots]) > trip_cap)) return;
   // count pass with a scratch list: the warp keeps each item's triplets, in
   // order and contiguous, in its own segment of `scratch`
   const bool keep = !WRITE && scratch != nullptr;
@@ -348,8 +351,20 @@ __global__ void __launch_bounds__(kSeedThreads)
 // warp per layer-0 hit.
 __global__ void k_seed_compact(const int* __restrict__ l0_cum, int n_events, const int* __restrict__ tcnt,
                                const int* __restrict__ toff, const int64_t* __restrict__ item_loc,
-                               const int4* __restrict__ scratch, int4* __restrict__ trip) {
+                               const int4* __restrict__ scratch, int4* __restrict__ trip,
+                               const int* __restrict__ overflow = nullptr, int64_t n_slots = 0,
+                               int64_t trip_cap = -1, int* __restrict__ status = nullptr) {
   const int lane = threadIdx.x & 31;
+  // launched without a host decision (fixed triplet capacity): nothing to do
+  // if a segment overflowed (the write pass searches again), and nothing is
+  // written if the list does not fit (capacity bit)
+  if (trip_cap >= 0) {
+    if (*(volatile const int*)overflow) return;
+    if (__ldg(&toff[n_slots]) > trip_cap) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, kStatCapacity);
+      return;
+    }
+  }
   const int n_items = __ldg(&l0_cum[n_events]);
   const int64_t n_warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); item < n_items;
@@ -367,13 +382,22 @@ __global__ void __launch_bounds__(kSeedThreads)
     k_seed_quads(const SeedArgs A, const float4* __restrict__ rec, const int* __restrict__ bin_off,
                  const int4* __restrict__ trip, int n_trip, int* __restrict__ qcnt, const int* __restrict__ qoff,
                  float* __restrict__ par, float* __restrict__ cov, int* __restrict__ hits, int* __restrict__ status,
-                 unsigned long long* __restrict__ stats) {
+                 unsigned long long* __restrict__ stats, const int* __restrict__ n_trip_dev = nullptr,
+                 int64_t stride = 0) {
   int st_l3 = 0, st_seeds = 0;   // work counters (count pass; per thread)
+  // with a fixed triplet capacity n_trip is that capacity and the list's
+  // length is read here (a list that did not fit is not searched)
+  if (n_trip_dev) {
+    const int64_t nt = __ldg(n_trip_dev);
+    if (nt > n_trip) return;
+    n_trip = (int)nt;
+  }
   const int64_t total = WRITE ? (int64_t)__ldg(&qoff[n_trip]) : 0;
   if (WRITE && total > A.max_seeds) {   // nothing is written; the caller sees the count
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, kStatCapacity);
     return;
   }
+  const int64_t cs = stride > 0 ? stride : total;   // column stride of par and cov
   const float R0 = A.R[0], R1 = A.R[1], R2 = A.R[2], R3 = A.R[3];
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_trip;
        j += (int64_t)gridDim.x * blockDim.x) {
@@ -410,11 +434,11 @@ __global__ void __launch_bounds__(kSeedThreads)
           // fixed diagonal covariance: beam spot, z0, 5 % in kappa (+ 0.01 /GeV), 5 mrad
           const float var[6] = {1e-4f, 1e-4f, 2.5e-3f, fmaf(2.5e-3f * kappa, kappa, 1e-4f), 2.5e-5f, 2.5e-5f};
 #pragma unroll
-          for (int k = 0; k < 6; ++k) par[k * total + i] = p6[k];
+          for (int k = 0; k < 6; ++k) par[k * cs + i] = p6[k];
 #pragma unroll
-          for (int k = 0; k < 21; ++k) cov[k * total + i] = 0.f;
+          for (int k = 0; k < 21; ++k) cov[k * cs + i] = 0.f;
 #pragma unroll
-          for (int k = 0; k < 6; ++k) cov[ci(k, k) * total + i] = var[k];
+          for (int k = 0; k < 6; ++k) cov[ci(k, k) * cs + i] = var[k];
           hits[4 * i] = a.orig;
           hits[4 * i + 1] = b.orig;
           hits[4 * i + 2] = c.orig;
@@ -496,10 +520,13 @@ __global__ void k_seed_l0_counts(const int* __restrict__ bin_off, int64_t bins_p
 // ev_seed_off[e] = qoff[poff[l0_cum[e]]], e = 0..E (all seeds of event e
 // come from its layer-0 hits, whose pairs come first in the pair list)
 __global__ void k_seed_event_off(const int* __restrict__ l0_cum, int n_events, const int* __restrict__ poff,
-                                 const int* __restrict__ qoff, int64_t* __restrict__ ev_seed_off) {
+                                 const int* __restrict__ qoff, int64_t q_len, int64_t* __restrict__ ev_seed_off) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e > n_events) return;
-  ev_seed_off[e] = qoff[poff[l0_cum[e]]];
+  // a triplet list longer than a fixed capacity was not searched (capacity bit
+  // set): its offsets are clamped to the scanned range
+  const int64_t j = poff[l0_cum[e]];
+  ev_seed_off[e] = qoff[j < q_len ? j : q_len];
 }
 
 }  // namespace
@@ -621,13 +648,16 @@ extern "C" mkf_status mkf_seed_tracks(mkf_ctx* ctx, float pt_min, float z_max, f
                                                              ctx->seed_scratch.as<int4>(), seg_cap,
                                                              ctx->seed_loc.as<int64_t>(), overflow);
   if ((e = launch_excl_scan(pcnt, H, poff, ctx->seed_part, st)) != cudaSuccess) return ctx->cuda_fail(e, "triplet scan");
+  const int64_t cap = ctx->seed_trip_cap;   // 0: size the triplet list from its count (one read-back)
   int n_trip = 0, over = 0;
-  if ((e = cudaMemcpyAsync(&n_trip, poff + H, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(&over, overflow, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-      (e = cudaStreamSynchronize(st)) != cudaSuccess)
-    return ctx->cuda_fail(e, "triplet count");
-  ctx->seed_trip_hint = n_trip;
-  const int64_t P = n_trip;
+  if (cap == 0) {
+    if ((e = cudaMemcpyAsync(&n_trip, poff + H, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&over, overflow, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+      return ctx->cuda_fail(e, "triplet count");
+    ctx->seed_trip_hint = n_trip;
+  }
+  const int64_t P = cap == 0 ? n_trip : cap;
   if ((e = ctx->seed_pairs.ensure((size_t)(P + 1) * sizeof(int4))) != cudaSuccess ||
       (e = ctx->seed_qcnt.ensure((size_t)(P + 1) * 4)) != cudaSuccess ||
       (e = ctx->seed_qoff.ensure((size_t)(P + 1) * 4)) != cudaSuccess)
@@ -635,22 +665,42 @@ extern "C" mkf_status mkf_seed_tracks(mkf_ctx* ctx, float pt_min, float z_max, f
   int4* trip = ctx->seed_pairs.as<int4>();
   int* qcnt = ctx->seed_qcnt.as<int>();
   int* qoff = ctx->seed_qoff.as<int>();
-  if (H > 0 && !over)   // scratch lists in place: move them
+  if (cap == 0) {
+    if (H > 0 && !over)   // scratch lists in place: move them
+      k_seed_compact<<<blocks, kSeedThreads, 0, st>>>(l0_cum, E, pcnt, poff, ctx->seed_loc.as<int64_t>(),
+                                                      ctx->seed_scratch.as<int4>(), trip);
+    else if (H > 0)        // a segment overflowed: search again and write
+      k_seed_triplets<true><<<blocks, kSeedThreads, 0, st>>>(A, rec, bin_off, l0_cum, H, nullptr, poff, trip, stats,
+                                                              nullptr, 0, nullptr, nullptr);
+  } else if (H > 0) {
+    // both launched; each decides on the device (overflow flag, triplet count)
     k_seed_compact<<<blocks, kSeedThreads, 0, st>>>(l0_cum, E, pcnt, poff, ctx->seed_loc.as<int64_t>(),
-                                                    ctx->seed_scratch.as<int4>(), trip);
-  else if (H > 0)        // a segment overflowed: search again and write
+                                                    ctx->seed_scratch.as<int4>(), trip, overflow, H, cap, status);
     k_seed_triplets<true><<<blocks, kSeedThreads, 0, st>>>(A, rec, bin_off, l0_cum, H, nullptr, poff, trip, stats,
-                                                            nullptr, 0, nullptr, nullptr);
+                                                            nullptr, 0, nullptr, overflow, cap);
+  }
   // stage 2 over the triplet list
+  const int* n_trip_dev = cap == 0 ? nullptr : poff + H;
+  const int64_t stride = cap == 0 ? 0 : max_seeds;
+  if (cap > 0 && (e = cudaMemsetAsync(qcnt, 0, (size_t)(P + 1) * 4, st)) != cudaSuccess)
+    return ctx->cuda_fail(e, "memset");
   if (P > 0)
     k_seed_quads<false><<<blocks, kSeedThreads, 0, st>>>(A, rec, bin_off, trip, (int)P, qcnt, nullptr, nullptr,
-                                                          nullptr, nullptr, status, stats);
+                                                          nullptr, nullptr, status, stats, n_trip_dev);
   if ((e = launch_excl_scan(qcnt, P, qoff, ctx->seed_part, st)) != cudaSuccess) return ctx->cuda_fail(e, "seed scan");
   if (P > 0)
     k_seed_quads<true><<<blocks, kSeedThreads, 0, st>>>(A, rec, bin_off, trip, (int)P, nullptr, qoff, seed_par,
-                                                         seed_cov, seed_hits, status, stats);
-  k_seed_event_off<<<(unsigned)((E + 1 + T - 1) / T), T, 0, st>>>(l0_cum, E, poff, qoff, ev_seed_off);
+                                                         seed_cov, seed_hits, status, stats, n_trip_dev, stride);
+  k_seed_event_off<<<(unsigned)((E + 1 + T - 1) / T), T, 0, st>>>(l0_cum, E, poff, qoff, P, ev_seed_off);
   if ((e = cudaGetLastError()) != cudaSuccess) return ctx->cuda_fail(e, "seeding");
+  return MKF_OK;
+}
+
+extern "C" mkf_status mkf_set_seed_config(mkf_ctx* ctx, int64_t max_triplets) {
+  if (!ctx) return MKF_ERR_ARG;
+  if (max_triplets < 0 || max_triplets >= (int64_t)INT32_MAX)
+    return ctx->fail(MKF_ERR_ARG, "max_triplets must be in 0..2^31-2");
+  ctx->seed_trip_cap = max_triplets;
   return MKF_OK;
 }
 

@@ -207,3 +207,79 @@ def test_event_without_layer0_hits_and_count_only():
     with pytest.raises(mkf.MkfError):
         mkf.mkf_sync(ctx)
     ctx.close()
+
+
+def test_seeding_build_fit_captured_in_one_graph():
+    """With a fixed triplet capacity, hit-based seeding reads nothing back, so
+    binning -> seeding -> building (n_seeds = max_seeds, the count taken from
+    ev_seed_off on the device) -> outward fit is captured as one CUDA graph.
+    Two replays equal the synchronous path (seeding with its read-back,
+    building the n seeds found, fitting them) on a six-event batch: the seeds,
+    the event offsets, the built tracks and the fit; rows past n are empty
+    tracks."""
+    import paper_2002_06295_gb300 as mkf
+    from tests._util import make_ctx
+    b = sev.make_batch(3)
+    evs = b.events[:6]
+    xyz = np.concatenate([e.hit_xyz for e in evs])
+    lcov = np.concatenate([e.hit_lcov for e in evs])
+    lay = np.concatenate([e.hit_layer for e in evs])
+    off = np.concatenate([[0], np.cumsum([e.n_hits for e in evs])])
+    dev = torch.device("cuda", 0)
+    t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(dev, dt)
+    X, Lc, Ly, O = t(xyz.T, torch.float32), t(lcov.T, torch.float32), t(lay, torch.int32), t(off, torch.int64)
+    kw = dict(chi2_cut=30.0, max_cands=4, max_holes=3, min_hits=4, dup_frac=0.5)
+    cap_seeds = 200000
+    # synchronous path
+    ctx = make_ctx(b.geom)
+    mkf.mkf_bin_hits(ctx, X, Lc, Ly, O)
+    s0 = mkf.mkf_seed_tracks(ctx, max_seeds=cap_seeds, **CUTS_B10)
+    n = s0["n"]
+    assert 1000 < n < cap_seeds
+    b0 = mkf.mkf_build_tracks(ctx, s0["par"].contiguous(), s0["cov"].contiguous(), s0["ev_seed_off"], **kw)
+    f0 = mkf.mkf_fit_tracks(ctx, X, Lc, Ly, b0["hits"], s0["par"].contiguous(), s0["cov"].contiguous())
+    mkf.mkf_sync(ctx)
+    ref = {k: v.cpu().numpy() for k, v in b0.items()}
+    fref = {k: v.cpu().numpy() for k, v in f0.items()}
+    seeds_ref = (s0["par"].cpu().numpy(), s0["hits"].cpu().numpy(), s0["ev_seed_off"].cpu().numpy())
+    # fixed capacity, no read-back: one graph
+    mkf.mkf_set_seed_config(ctx, 4 * int(off[-1]))
+    sbuf = dict(par=torch.zeros(6 * cap_seeds, device=dev), cov=torch.zeros(21 * cap_seeds, device=dev),
+                hits=torch.zeros(4 * cap_seeds, dtype=torch.int32, device=dev),
+                ev_seed_off=torch.zeros(len(evs) + 1, dtype=torch.int64, device=dev))
+    bout = mkf.alloc_build_outputs(ctx, cap_seeds)
+    fout = dict(par=torch.empty((6, cap_seeds), device=dev), cov=torch.empty((21, cap_seeds), device=dev),
+                chi2=torch.empty(cap_seeds, device=dev), ok=torch.empty(cap_seeds, dtype=torch.int32, device=dev))
+
+    def step():
+        mkf.mkf_bin_hits(ctx, X, Lc, Ly, O)
+        s = mkf.mkf_seed_tracks(ctx, out=sbuf, read_count=False, **CUTS_B10)
+        mkf.mkf_build_tracks(ctx, s["par"], s["cov"], s["ev_seed_off"], out=bout, **kw)
+        mkf.mkf_fit_tracks(ctx, X, Lc, Ly, bout["hits"], s["par"], s["cov"], out=fout)
+
+    step()   # sizes the workspace outside the capture
+    torch.cuda.synchronize()
+    mkf.mkf_sync(ctx)
+    mkf.mkf_set_timing(ctx, False)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step()
+    for _ in range(2):
+        for v in bout.values():
+            v.fill_(7)
+        g.replay()
+        torch.cuda.synchronize()
+        mkf.mkf_sync(ctx)
+        assert np.array_equal(sbuf["ev_seed_off"].cpu().numpy(), seeds_ref[2])
+        par = sbuf["par"].view(6, cap_seeds).cpu().numpy()
+        assert np.array_equal(par[:, :n], seeds_ref[0])
+        assert np.array_equal(sbuf["hits"].view(cap_seeds, 4).cpu().numpy()[:n], seeds_ref[1])
+        got = {k: v.cpu().numpy() for k, v in bout.items()}
+        for k in ("hits", "flags", "score"):
+            assert np.array_equal(got[k][:n], ref[k]), k
+        assert np.array_equal(got["par"][:, :n], ref["par"])
+        assert (got["hits"][n:] == -1).all() and (got["flags"][n:] == mkf.TRK_SHORT).all()
+        fgot = {k: v.cpu().numpy() for k, v in fout.items()}
+        assert np.array_equal(fgot["par"][:, :n], fref["par"])
+        assert np.array_equal(fgot["chi2"][:n], fref["chi2"])
+    ctx.close()
