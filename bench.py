@@ -442,6 +442,49 @@ def measure_seeding(mkf, dev, reps=5):
     mkf.mkf_sync(ctx)
     w = mkf.mkf_get_seed_stats(ctx)
     peak = fp32_peak(dev)
+    # the seeded path as one CUDA graph: binning, seeding with a fixed triplet
+    # capacity (no read-back), building the seeds found (count read on the
+    # device), outward fit of the built tracks
+    graph_ms = None
+    try:
+        cap = int(o["hits"].numel()) // 4
+        mkf.mkf_set_seed_config(ctx, 4 * int(b.hit_off[-1]))
+        X, Lc, Ly, O = (t(xyz.T, torch.float32), t(lcov.T, torch.float32), t(lay, torch.int32),
+                        t(b.hit_off, torch.int64))
+        sbuf = dict(par=torch.zeros(6 * cap, device=dev), cov=torch.zeros(21 * cap, device=dev),
+                    hits=torch.zeros(4 * cap, dtype=torch.int32, device=dev),
+                    ev_seed_off=torch.zeros(b.n_events + 1, dtype=torch.int64, device=dev))
+        bout = mkf.alloc_build_outputs(ctx, cap)
+        fout = dict(par=torch.empty((6, cap), device=dev), cov=torch.empty((21, cap), device=dev),
+                    chi2=torch.empty(cap, device=dev), ok=torch.empty(cap, dtype=torch.int32, device=dev))
+        bkw = dict(chi2_cut=30.0, max_cands=4, max_holes=3, min_hits=4, dup_frac=0.5)
+
+        def seeded_step():
+            mkf.mkf_bin_hits(ctx, X, Lc, Ly, O)
+            sd = mkf.mkf_seed_tracks(ctx, out=sbuf, read_count=False, **cuts)
+            mkf.mkf_build_tracks(ctx, sd["par"], sd["cov"], sd["ev_seed_off"], out=bout, **bkw)
+            mkf.mkf_fit_tracks(ctx, X, Lc, Ly, bout["hits"], sd["par"], sd["cov"], out=fout)
+
+        seeded_step()
+        torch.cuda.synchronize()
+        mkf.mkf_sync(ctx)
+        mkf.mkf_set_timing(ctx, False)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            seeded_step()
+        gts = []
+        for r in range(reps + 1):
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            graph.replay()
+            e.record(stream)
+            e.synchronize()
+            if r:
+                gts.append(a.elapsed_time(e))
+        mkf.mkf_sync(ctx)
+        graph_ms = min(gts)
+    except Exception as exc:   # reported, not fatal to the other lines
+        graph_ms = "%s: %s" % (type(exc).__name__, str(exc).splitlines()[0][:160])
     ctx.close()
     ms = min(ts)
     flops = (w["l1_examined"] * FLOPS_SEED_L1 + w["pairs"] * FLOPS_SEED_PAIR + w["l2_examined"] * FLOPS_SEED_L2
@@ -454,6 +497,9 @@ def measure_seeding(mkf, dev, reps=5):
     return {"workload": "C3: 256 events of the 10-cylinder barrel, %d hits, %d true tracks; cuts %s"
                         % (int(b.hit_off[-1]), int(b.seed_off[-1]), cuts),
             "ms": ms, "events_per_s": b.n_events / (ms * 1e-3), "seeds": int(o["n"]),
+            "seeded_build_fit_graph_ms": graph_ms,
+            "seeded_build_fit_graph_events_per_s": (b.n_events / (graph_ms * 1e-3)
+                                                    if isinstance(graph_ms, float) else None),
             "seeds_per_s": o["n"] / (ms * 1e-3), "work": w,
             "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                          "frac": ach / peak,

@@ -341,10 +341,10 @@ mkf_status mkf_dedup_tracks(mkf_ctx* ctx, const int* hits, int L, const float* s
  * stays alive: do not call this entry point again after cudaDeviceReset.  All
  * calls share the array: calls whose work can overlap on the GPU race and must
  * be serialised by the caller.  Device-side problems are written as MKF status
- * bits to out_status (DEVICE int, cleared by the call; may be NULL): 1
- * capacity, 2 resolution did not converge, 4 an input index out of range (a
- * hit id, or an event offset outside 0..n_seeds, which is clamped into that
- * range so that nothing is read or written past the track arrays). */
+ * bits to out_status (DEVICE int, cleared by the call; may be NULL): 2
+ * resolution did not converge, 4 an input index out of range (a hit id, or an
+ * event offset outside 0..n_seeds, which is clamped into that range so that
+ * nothing is read or written past the track arrays). */
 mkf_status mkf_dedup_tracks_noalloc(const int* hits, int L, const float* score, const int* nhits,
                                     const int64_t* ev_seed_off, int n_events, int64_t n_seeds, int64_t n_hits_total,
                                     int min_hits, float dup_frac, int* out_flags, int* out_status, void* stream);

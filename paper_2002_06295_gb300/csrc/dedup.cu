@@ -18,7 +18,6 @@ namespace mkf {
 
 namespace {
 
-constexpr int kMaxNeighbours = 64;   // distinct tracks sharing a hit with one track
 constexpr int kMaxBeaters = 32;      // conflicting better-ranked tracks kept per track
 
 __global__ void k_dd_link(const int* __restrict__ hits, int L, const int* __restrict__ nhits, int64_t n_seeds,
@@ -41,53 +40,64 @@ __global__ void k_dd_link(const int* __restrict__ hits, int L, const int* __rest
 
 __device__ __forceinline__ bool beats(float sb, int b, float sa, int a) { return sb > sa || (sb == sa && b < a); }
 
-__global__ void k_dd_conflicts(const int* __restrict__ hits, int L, const float* __restrict__ score,
-                               const int* __restrict__ nhits, int64_t n_seeds, int64_t n_hits, int min_hits,
-                               float dup_frac, const int* __restrict__ head, const int* __restrict__ next,
-                               int* __restrict__ beat, int* __restrict__ nbeat, int* __restrict__ status) {
-  const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (a >= n_seeds) return;
-  nbeat[a] = 0;
+// Calls f(b) for every beater b of track a: a track that shares more than
+// dup_frac * min(n_a, n_b) hits with a and ranks higher.  Every track b that
+// shares a hit with a is met through the hit -> track lists; the pair is
+// taken once, at a's first hit that b also holds, where the shared hits are
+// counted directly from both rows.  Nothing is stored per neighbour, so any
+// number of tracks may share a's hits.  f returns false to stop early.
+template <class F>
+__device__ __forceinline__ void for_each_beater(int64_t a, const int* __restrict__ hits, int L,
+                                                const float* __restrict__ score, const int* __restrict__ nhits,
+                                                int64_t n_hits, float dup_frac, const int* __restrict__ head,
+                                                const int* __restrict__ next, F f) {
+  const int* ra = hits + a * L;
   const int na = nhits[a];
-  if (na < min_hits) return;
-  int nb_id[kMaxNeighbours];
-  int nb_ct[kMaxNeighbours];
-  int n = 0;
-  bool overflow = false;
+  const float sa = score[a];
   for (int k = 0; k < L; ++k) {
-    const int h = hits[a * L + k];
+    const int h = ra[k];
     if (h < 0 || h >= n_hits) continue;
     for (int pr = head[h]; pr >= 0; pr = next[pr]) {
       const int b = pr / L;
       if (b == a) continue;
-      int j = 0;
-      while (j < n && nb_id[j] != b) ++j;
-      if (j < n) {
-        ++nb_ct[j];
-      } else if (n < kMaxNeighbours) {
-        nb_id[n] = b;
-        nb_ct[n] = 1;
-        ++n;
-      } else {
-        overflow = true;
+      const int* rb = hits + (int64_t)b * L;
+      int shared = 0, first = L;
+      for (int j = 0; j < L; ++j) {
+        const int hj = ra[j];
+        if (hj < 0 || hj >= n_hits) continue;
+        bool in_b = false;
+        for (int q = 0; q < L && !in_b; ++q) in_b = rb[q] == hj;
+        if (in_b) {
+          ++shared;
+          first = j < first ? j : first;
+        }
       }
+      if (first != k) continue;   // taken at an earlier hit of a
+      const int nmin = min(na, nhits[b]);
+      if ((float)shared > dup_frac * (float)nmin && beats(score[b], b, sa, (int)a))
+        if (!f(b)) return;
     }
   }
-  const float sa = score[a];
+}
+
+// Beaters of each track: up to kMaxBeaters are listed; a track with more is
+// marked (nbeat = -1) and the resolution finds its beaters again from the
+// hit -> track lists each time it looks at it.
+__global__ void k_dd_conflicts(const int* __restrict__ hits, int L, const float* __restrict__ score,
+                               const int* __restrict__ nhits, int64_t n_seeds, int64_t n_hits, int min_hits,
+                               float dup_frac, const int* __restrict__ head, const int* __restrict__ next,
+                               int* __restrict__ beat, int* __restrict__ nbeat) {
+  const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n_seeds) return;
+  nbeat[a] = 0;
+  if (nhits[a] < min_hits) return;
   int m = 0;
-  for (int j = 0; j < n; ++j) {
-    const int b = nb_id[j];
-    const int nmin = min(na, nhits[b]);
-    if ((float)nb_ct[j] > dup_frac * (float)nmin && beats(score[b], b, sa, (int)a)) {
-      if (m < kMaxBeaters)
-        beat[a * kMaxBeaters + m] = b;
-      else
-        overflow = true;
-      ++m;
-    }
-  }
-  nbeat[a] = min(m, kMaxBeaters);
-  if (overflow) atomicOr(status, kStatCapacity);
+  for_each_beater(a, hits, L, score, nhits, n_hits, dup_frac, head, next, [&](int b) {
+    if (m < kMaxBeaters) beat[a * kMaxBeaters + m] = b;
+    ++m;
+    return m <= kMaxBeaters;
+  });
+  nbeat[a] = m <= kMaxBeaters ? m : -1;
 }
 
 // state: 0 undecided, 1 kept, 2 duplicate, 3 short.  The event offsets come
@@ -97,7 +107,9 @@ __global__ void k_dd_conflicts(const int* __restrict__ hits, int L, const float*
 __global__ void k_dd_resolve(const int64_t* __restrict__ ev_seed_off, int64_t n_seeds, const int* __restrict__ nhits,
                              int min_hits, const int* __restrict__ beat, const int* __restrict__ nbeat, int* state,
                              int* __restrict__ out_flags, unsigned long long* __restrict__ stats,
-                             int* __restrict__ status) {
+                             int* __restrict__ status, const int* __restrict__ hits, int L,
+                             const float* __restrict__ score, int64_t n_hits, float dup_frac,
+                             const int* __restrict__ head, const int* __restrict__ next) {
   const int64_t r0 = ev_seed_off[blockIdx.x], r1 = ev_seed_off[blockIdx.x + 1];
   const int64_t s0 = r0 < 0 ? 0 : (r0 > n_seeds ? n_seeds : r0);
   const int64_t s1 = r1 < s0 ? s0 : (r1 > n_seeds ? n_seeds : r1);
@@ -113,13 +125,22 @@ __global__ void k_dd_resolve(const int64_t* __restrict__ ev_seed_off, int64_t n_
       if (vs[a] != 0) continue;
       bool any_kept = false, all_done = true;
       const int nb = nbeat[a];
-      for (int j = 0; j < nb; ++j) {
-        const int sb = vs[beat[a * kMaxBeaters + j]];
-        if (sb == 1) {
-          any_kept = true;
-          break;
+      if (nb >= 0) {
+        for (int j = 0; j < nb; ++j) {
+          const int sb = vs[beat[a * kMaxBeaters + j]];
+          if (sb == 1) {
+            any_kept = true;
+            break;
+          }
+          if (sb == 0) all_done = false;
         }
-        if (sb == 0) all_done = false;
+      } else {
+        for_each_beater(a, hits, L, score, nhits, n_hits, dup_frac, head, next, [&](int b) {
+          const int sb = vs[b];
+          if (sb == 1) any_kept = true;
+          if (sb == 0) all_done = false;
+          return !any_kept;
+        });
       }
       if (any_kept) {
         vs[a] = 2;
@@ -172,10 +193,12 @@ cudaError_t launch_dedup(mkf_ctx* ctx, const int* hits, int L, const float* scor
                               ctx->dd_next.as<int>(), status);
   k_dd_conflicts<<<gs, T, 0, st>>>(hits, L, score, nhits, n_seeds, n_hits_total, min_hits, dup_frac,
                                    ctx->dd_head.as<int>(), ctx->dd_next.as<int>(), ctx->dd_beat.as<int>(),
-                                   ctx->dd_nbeat.as<int>(), status);
+                                   ctx->dd_nbeat.as<int>());
   k_dd_resolve<<<(unsigned)n_events, 1024, 0, st>>>(ev_seed_off, n_seeds, nhits, min_hits, ctx->dd_beat.as<int>(),
                                                     ctx->dd_nbeat.as<int>(), ctx->dd_state.as<int>(), out_flags,
-                                                    ctx->stats.as<unsigned long long>(), status);
+                                                    ctx->stats.as<unsigned long long>(), status, hits, L, score,
+                                                    n_hits_total, dup_frac, ctx->dd_head.as<int>(),
+                                                    ctx->dd_next.as<int>());
   ctx->tock(kTDedup, st);
   return cudaGetLastError();
 }
@@ -269,8 +292,9 @@ extern "C" mkf_status mkf_dedup_tracks_noalloc(const int* hits, int L, const flo
   const unsigned gs = (unsigned)((n_seeds + T - 1) / T);
   k_dd_link<<<gs, T, 0, st>>>(hits, L, nhits, n_seeds, n_hits_total, min_hits, head, next, status);
   k_dd_conflicts<<<gs, T, 0, st>>>(hits, L, score, nhits, n_seeds, n_hits_total, min_hits, dup_frac, head, next, beat,
-                                   nbeat, status);
+                                   nbeat);
   k_dd_resolve<<<(unsigned)n_events, 1024, 0, st>>>(ev_seed_off, n_seeds, nhits, min_hits, beat, nbeat, state,
-                                                    out_flags, nullptr, status);
+                                                    out_flags, nullptr, status, hits, L, score, n_hits_total,
+                                                    dup_frac, head, next);
   return cudaGetLastError() == cudaSuccess ? MKF_OK : MKF_ERR_CUDA;
 }
