@@ -44,10 +44,15 @@ UNIT = "cand-steps/s"
 # add/mul/div = 1; sqrt, rsqrt, sin/cos, atan, log not counted); barrel-surface
 # counts, so disk-heavy work is under-counted
 FLOPS_NAV_TEST = 44       # one surface tested by the navigation (crossing path + acceptance)
-FLOPS_CAND_STEP = 600     # helix 46 + Jacobian 84 + J C J^T 408 + material 25 + window ~35
+# one candidate step: helix 46 + Jacobian 84 + material 25 + window ~35 + the
+# U-D transport 676 (J U rows 120, the theta row 17, Gram-Schmidt of rows 4..0
+# 455, position covariance 84)
+FLOPS_CAND_STEP = 866
 FLOPS_BOX = 7             # one candidate-hit pair examined: residuals r_a, r_b + half-plane test
 FLOPS_CHI2 = 33           # rest of the chi2 of a pair that passes the box test (with the Cauchy-Schwarz floor)
-FLOPS_UPDATE = 625        # one Kalman update of a kept child, Joseph-form covariance
+# one Kalman update of a kept child: two Bierman scalar updates (140 each) and
+# the hit covariance's decorrelation, rows and residuals (21)
+FLOPS_UPDATE = 301
 FP32_LANES = 128          # per SM (Blackwell)
 
 

@@ -18,6 +18,7 @@ namespace mkf {
 
 namespace {
 
+constexpr int kMaxNeighbours = 64;   // distinct tracks sharing a hit with one track, listed
 constexpr int kMaxBeaters = 32;      // conflicting better-ranked tracks kept per track
 
 __global__ void k_dd_link(const int* __restrict__ hits, int L, const int* __restrict__ nhits, int64_t n_seeds,
@@ -44,8 +45,9 @@ __device__ __forceinline__ bool beats(float sb, int b, float sa, int a) { return
 // dup_frac * min(n_a, n_b) hits with a and ranks higher.  Every track b that
 // shares a hit with a is met through the hit -> track lists; the pair is
 // taken once, at a's first hit that b also holds, where the shared hits are
-// counted directly from both rows.  Nothing is stored per neighbour, so any
-// number of tracks may share a's hits.  f returns false to stop early.
+// counted directly from both rows (L^2 compares).  Nothing is stored per
+// neighbour, so any number of tracks may share a's hits.  f returns false to
+// stop early.
 template <class F>
 __device__ __forceinline__ void for_each_beater(int64_t a, const int* __restrict__ hits, int L,
                                                 const float* __restrict__ score, const int* __restrict__ nhits,
@@ -80,9 +82,13 @@ __device__ __forceinline__ void for_each_beater(int64_t a, const int* __restrict
   }
 }
 
-// Beaters of each track: up to kMaxBeaters are listed; a track with more is
-// marked (nbeat = -1) and the resolution finds its beaters again from the
-// hit -> track lists each time it looks at it.
+// Beaters of each track from its neighbours: every track sharing a hit with
+// it is met through the hit -> track lists and its shared hits counted in a
+// short list.  A track with more than kMaxNeighbours neighbours or
+// kMaxBeaters beaters is marked (nbeat = -1): the resolution then derives its
+// beaters again with for_each_beater, which stores nothing per neighbour, each
+// time it looks at it.  So no input overflows; the marked tracks (tens of the
+// 1.4 M of a hit-seeded batch) only cost more.
 __global__ void k_dd_conflicts(const int* __restrict__ hits, int L, const float* __restrict__ score,
                                const int* __restrict__ nhits, int64_t n_seeds, int64_t n_hits, int min_hits,
                                float dup_frac, const int* __restrict__ head, const int* __restrict__ next,
@@ -90,14 +96,46 @@ __global__ void k_dd_conflicts(const int* __restrict__ hits, int L, const float*
   const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= n_seeds) return;
   nbeat[a] = 0;
-  if (nhits[a] < min_hits) return;
+  const int na = nhits[a];
+  if (na < min_hits) return;
+  int nb_id[kMaxNeighbours];
+  int nb_ct[kMaxNeighbours];
+  int n = 0;
+  bool overflow = false;
+  for (int k = 0; k < L && !overflow; ++k) {
+    const int h = hits[a * L + k];
+    if (h < 0 || h >= n_hits) continue;
+    for (int pr = head[h]; pr >= 0; pr = next[pr]) {
+      const int b = pr / L;
+      if (b == a) continue;
+      int j = 0;
+      while (j < n && nb_id[j] != b) ++j;
+      if (j < n) {
+        ++nb_ct[j];
+      } else if (n < kMaxNeighbours) {
+        nb_id[n] = b;
+        nb_ct[n] = 1;
+        ++n;
+      } else {
+        overflow = true;
+        break;
+      }
+    }
+  }
+  const float sa = score[a];
   int m = 0;
-  for_each_beater(a, hits, L, score, nhits, n_hits, dup_frac, head, next, [&](int b) {
-    if (m < kMaxBeaters) beat[a * kMaxBeaters + m] = b;
-    ++m;
-    return m <= kMaxBeaters;
-  });
-  nbeat[a] = m <= kMaxBeaters ? m : -1;
+  for (int j = 0; j < n && !overflow; ++j) {
+    const int b = nb_id[j];
+    const int nmin = min(na, nhits[b]);
+    if ((float)nb_ct[j] > dup_frac * (float)nmin && beats(score[b], b, sa, (int)a)) {
+      if (m < kMaxBeaters)
+        beat[a * kMaxBeaters + m] = b;
+      else
+        overflow = true;
+      ++m;
+    }
+  }
+  nbeat[a] = overflow ? -1 : m;
 }
 
 // state: 0 undecided, 1 kept, 2 duplicate, 3 short.  The event offsets come

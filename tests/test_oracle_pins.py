@@ -72,6 +72,24 @@ def test_highland_width_at_hand_computed_points(orc, case):
     assert np.all(d[others] == 0.0)
 
 
+def test_joseph_update_keeps_realistic_fits_psd(orc):
+    """The outward fits of the C2 event's true-hit tracks (pixel hits, strip
+    disks with sigma_r / sigma_rphi = 333, fits that fail for loopers) end with
+    covariances whose eigenvalues are >= -1e-12 of their trace: the Joseph-form
+    update is a sum of positive semi-definite terms (the plain C - K R K^T left
+    four of these indefinite)."""
+    ev = synth.make_config_event(2)
+    geo = geo_of(ev.geom)
+    sel = (ev.true_hits >= 0).sum(1) >= 6
+    _, cov, _, ok = orc.fit(geo, ev.hit_xyz, ev.hit_lcov, ev.hit_layer, ev.true_hits[sel], ev.seed_par[sel],
+                            ev.seed_cov[sel])
+    M = orc.unpack_cov(cov[ok == 1])
+    w = np.linalg.eigvalsh(M)
+    tr = np.trace(M, axis1=1, axis2=2)
+    assert sel.sum() > 4000
+    assert np.all(w[:, 0] >= -1e-12 * tr)
+
+
 # --- helix closed forms ------------------------------------------------------
 
 def test_helix_closure(orc):
