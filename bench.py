@@ -69,7 +69,7 @@ def parse():
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c5"],
                     help="timed workload (c2: the CMS-like event the metric is quoted on)")
     ap.add_argument("--no-graph", action="store_true", help="time eager launches only (no CUDA-graph replay)")
-    ap.add_argument("--only", choices=["strips", "seeding", "overlaps"],
+    ap.add_argument("--only", choices=["strips", "seeding", "overlaps", "in_flight"],
                     help="run one secondary measurement alone and print it (for profiling its kernel)")
     return ap.parse_args()
 
@@ -309,6 +309,115 @@ def measure_batched(mkf, tune, dev, reps=3):
             "batched_cand_steps_per_s": steps / (bms * 1e-3),
             "tuned_batched": {k: tb[k] for k in ("n_phi", "n_w", "warps", "lanes")},
             "tuned_plain": {k: tp[k] for k in ("n_phi", "n_w", "warps", "lanes")}}
+
+
+def measure_in_flight(mkf, dev, counts=(1, 2, 4), rounds=20):
+    """C2 events in flight: S distinct C2 events (event seeds 0..S-1), each
+    with its own context, stream and captured CUDA graph of the whole step
+    (binning -> building -> dedup -> forward fit -> adjoint beside the inward
+    fit), started together after an L2 flush; a round ends when all S are
+    done.  The step and the events are those of the C2 headline; only the
+    number of events on the GPU at once changes (the paper's throughput runs
+    likewise give each thread its own event)."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2002_06295_gb300 import tune
+    spec = synth.WORKLOAD_SPECS[2]
+    kw = dict(chi2_cut=spec["chi2_cut"], max_cands=spec["max_cands"], max_holes=spec["max_holes"],
+              min_hits=spec["min_hits"], dup_frac=spec["dup_frac"])
+
+    def make(e):
+        ev = synth.make_config_event(2, e)
+        g = ev.geom
+        ctx = mkf.Context(dev.index)
+        mkf.mkf_load_geometry(ctx, g.table(), g.bz, 64, 16)
+        t = lambda a, dt=torch.float32: torch.tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+        d = dict(xyz=t(ev.hit_xyz.T), lcov=t(ev.hit_lcov.T), layer=t(ev.hit_layer, torch.int32),
+                 hoff=t([0, ev.n_hits], torch.int64), sp=t(ev.seed_par.T), sc=t(ev.seed_cov.T),
+                 soff=t([0, ev.n_seeds], torch.int64))
+        tune.autotune_build(ctx, g.table(), g.bz, d["xyz"], d["lcov"], d["layer"], d["hoff"], d["sp"], d["sc"],
+                            d["soff"], **kw)
+        S, L = ev.n_seeds, g.n_layers
+        out = mkf.alloc_build_outputs(ctx, S)
+        ckpt = torch.empty((L, 27, S), device=dev)
+        res = lambda: dict(par=torch.empty((6, S), device=dev), cov=torch.empty((21, S), device=dev),
+                           chi2=torch.empty(S, device=dev), ok=torch.empty(S, dtype=torch.int32, device=dev))
+        fit_out, bwd_out = res(), res()
+        g_chi2 = torch.ones(S, device=dev)
+        adj = dict(g_hit=torch.empty((3, ev.n_hits), device=dev), g_align=torch.empty((L, 3), device=dev),
+                   g_x0=torch.empty(L, device=dev))
+        main, side = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+        fwd_done, bwd_done = torch.cuda.Event(), torch.cuda.Event()
+
+        def step():
+            mkf.mkf_bin_hits(ctx, d["xyz"], d["lcov"], d["layer"], d["hoff"])
+            mkf.mkf_build_tracks(ctx, d["sp"], d["sc"], d["soff"], out=out, **kw)
+            mkf.mkf_fit_tracks(ctx, d["xyz"], d["lcov"], d["layer"], out["hits"], d["sp"], d["sc"], ckpt=ckpt,
+                               out=fit_out)
+            cur = torch.cuda.current_stream()
+            fwd_done.record(cur)
+            side.wait_event(fwd_done)
+            mkf.mkf_fit_backward(ctx, d["xyz"], d["lcov"], d["layer"], out["hits"], fit_out["par"], out=bwd_out,
+                                 stream=side)
+            bwd_done.record(side)
+            mkf.mkf_fit_tracks_adjoint(ctx, d["xyz"], d["lcov"], d["layer"], out["hits"], d["sp"], d["sc"], ckpt,
+                                       g_chi2=g_chi2, out=adj)
+            cur.wait_event(bwd_done)
+
+        with torch.cuda.stream(main):
+            for _ in range(3):
+                step()
+        torch.cuda.synchronize()
+        mkf.mkf_sync(ctx)
+        units = mkf.mkf_get_stats(ctx)["cand_steps"]   # counters of the last build call
+        cg = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(main):
+            with torch.cuda.graph(cg, stream=main):
+                step()
+        torch.cuda.synchronize()
+        return dict(ctx=ctx, graph=cg, stream=main, units=units, keep=(d, out, ckpt, fit_out, bwd_out, adj, side))
+
+    items = [make(e) for e in range(max(counts))]
+    flush = torch.empty(256 * 1024 * 1024 // 4, device=dev)   # > 129 MB L2
+    base = torch.cuda.current_stream()
+    per = {}
+    for n in counts:
+        its = items[:n]
+        for _ in range(3):
+            for it in its:
+                with torch.cuda.stream(it["stream"]):
+                    it["graph"].replay()
+        torch.cuda.synchronize()
+        times = []
+        for r in range(rounds):
+            flush.fill_(float(r))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(base)
+            ends = []
+            for it in its:
+                it["stream"].wait_event(a)
+                with torch.cuda.stream(it["stream"]):
+                    it["graph"].replay()
+                e = torch.cuda.Event()
+                e.record(it["stream"])
+                ends.append(e)
+            for e in ends:
+                base.wait_event(e)
+            b.record(base)
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b))
+        units = sum(it["units"] for it in its)
+        total = sum(times)
+        per[str(n)] = {"ms_per_round": total / rounds, "ms_per_event": total / rounds / n,
+                       "value": units * rounds / (total * 1e-3), "events_per_s": n * rounds / (total * 1e-3),
+                       "gpu_launches": LAUNCHES_PER_STEP * n * rounds}
+    for it in items:
+        it["graph"] = None
+        it["ctx"].close()
+    return {"workload": "C2 step, S distinct C2 events in flight (one context, stream and CUDA graph each)",
+            "unit": UNIT, "l2": "flushed (256 MB write) between rounds", "rounds": rounds, "by_events_in_flight": per}
 
 
 def measure_fit_gradient(mkf, dev, reps=3):
@@ -921,7 +1030,8 @@ def main():
     if args.only:
         import paper_2002_06295_gb300 as mkf_only
         dev_only = torch.device("cuda", local)
-        fn = {"strips": measure_strips, "seeding": measure_seeding, "overlaps": measure_overlaps}[args.only]
+        fn = {"strips": measure_strips, "seeding": measure_seeding, "overlaps": measure_overlaps,
+              "in_flight": measure_in_flight}[args.only]
         print(json.dumps({args.only: fn(mkf_only, dev_only)}), flush=True)
         return
     dist = None
@@ -971,6 +1081,8 @@ def main():
             secondary["stress_c5"] = path_summary(
                 time_path(mkf, dev, workload_events(synth, 5, 0), synth.WORKLOAD_SPECS[5], min(args.steps, 5), 3),
                 "c5", dev)
+        if args.workload == "c2":
+            secondary["c2_in_flight"] = measure_in_flight(mkf, dev)
         secondary["c1_event"] = c1_latency(
             time_path(mkf, dev, workload_events(synth, 1, 0), synth.WORKLOAD_SPECS[1], 50, 5))
         secondary.update({"batched_vs_plain": measure_batched(mkf, _tune, dev),
