@@ -1,0 +1,135 @@
+"""The stress configuration at full size: 64 events x 10000 tracks of the
+10-cylinder barrel (pT down to 0.3 GeV, |eta| < 2.5, 50 % noise hits,
+8 candidates per seed) built in one launch in the launch shape and binning
+the autotuner picks (as the benchmark does), then the outward and inward refit
+of every found track.  Sampled results are compared with the oracle:
+building on seeds spread over all events, the refits on tracks spread over
+all events (the oracle fits the same hit lists from the same starting
+states)."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from _util import (CHI2_RTOL, COV_RTOL, PAR_RTOL, compare, cov_rel_err, f32, gpu_build, i32, make_ctx,
+                   oracle_build, par_rel_err)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+@pytest.fixture(scope="module")
+def stress():
+    """The full batch, built once in the autotuned shape; float32-rounded
+    inputs so that both sides fit the same numbers."""
+    import paper_2002_06295_gb300 as mkf
+    from paper_2002_06295_gb300 import tune
+    b = synth.make_batch(5)
+    q = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    for ev in b.events:
+        ev.hit_xyz, ev.hit_lcov = q(ev.hit_xyz), q(ev.hit_lcov)
+        ev.seed_par, ev.seed_cov = q(ev.seed_par), q(ev.seed_cov)
+    spec = synth.WORKLOAD_SPECS[5]
+    dev = torch.device("cuda", 0)
+    ctx = make_ctx(b.geom)
+    xyz, lcov, lay = b.cat("hit_xyz"), b.cat("hit_lcov"), b.cat("hit_layer")
+    sp, sc = b.cat("seed_par"), b.cat("seed_cov")
+    tuned = tune.autotune_build(ctx, b.geom.table(), b.geom.bz, f32(xyz.T, dev), f32(lcov.T, dev), i32(lay, dev),
+                                torch.tensor(b.hit_off, device=dev), f32(sp.T, dev), f32(sc.T, dev),
+                                torch.tensor(b.seed_off, device=dev), max_cands=spec["max_cands"],
+                                chi2_cut=spec["chi2_cut"], max_holes=spec["max_holes"], min_hits=spec["min_hits"],
+                                dup_frac=spec["dup_frac"])
+    g = gpu_build(ctx, b.events, max_cands=spec["max_cands"], chi2_cut=spec["chi2_cut"],
+                  max_holes=spec["max_holes"], min_hits=spec["min_hits"], dup_frac=spec["dup_frac"])
+    yield dict(b=b, ctx=ctx, g=g, spec=spec, tuned=tuned, xyz=xyz, lcov=lcov, lay=lay, sp=sp, sc=sc)
+    ctx.close()
+
+
+def test_full_batch_building_sampled_seeds(stress):
+    """160 seeds spread over the 64 events against the oracle run on their
+    own event: exact hit lists, counts and scores outside the 1e-4 margins,
+    parameters and covariances within 1e-4."""
+    b, g, spec = stress["b"], stress["g"], stress["spec"]
+    S = int(b.seed_off[-1])
+    assert g["hits"].shape[0] == S and g["stats"]["seeds"] == S
+    rng = np.random.default_rng(21)
+    pick = np.sort(rng.choice(S, 160, replace=False))
+    ev_of = np.searchsorted(b.seed_off, pick, side="right") - 1
+    tot = dict(n=0, robust=0, fragile=0)
+    for e in np.unique(ev_of):
+        ev = b.events[e]
+        loc = pick[ev_of == e] - b.seed_off[e]
+        r = oracle_build([ev], max_cands=spec["max_cands"], chi2_cut=spec["chi2_cut"], max_holes=spec["max_holes"],
+                         min_hits=spec["min_hits"], seeds=loc, dedup=False)
+        off, hb = int(b.seed_off[e]), int(b.hit_off[e])
+        gi = {k: (v[off:off + ev.n_seeds] if isinstance(v, np.ndarray) and v.shape[:1] == (S,) else v)
+              for k, v in g.items()}
+        gi["hits"] = np.where(gi["hits"] >= 0, gi["hits"] - hb, -1)
+        rep = compare(gi, r, sel=loc)
+        assert rep["mismatch_robust"] == 0, rep
+        if "par_err" in rep:
+            assert rep["par_err"] < PAR_RTOL, rep
+            assert rep["cov_err"] < COV_RTOL, rep
+        for k in tot:
+            tot[k] += rep[k]
+    print("C5 full batch, sampled seeds:", tot, "launch", stress["tuned"])
+    # forward low-pT tracks with few hits carry correlations near 1
+    assert tot["fragile"] <= 0.3 * tot["n"]
+
+
+def test_full_batch_refit_sampled_tracks(stress):
+    """Outward fit (with checkpoints, as the step runs it) of every built track
+    of the batch in one launch; 200 tracks of at least 4 hits spread over the
+    events against the oracle's fit of the same hit lists: parameters and
+    covariances within 1e-4, chi2 within 1e-3.  Then the inward fit of every
+    track in one launch, the sampled tracks starting from the oracle's outward
+    result, against the oracle's inward fit."""
+    import oracle
+    import paper_2002_06295_gb300 as mkf
+    b, g, ctx = stress["b"], stress["g"], stress["ctx"]
+    dev = torch.device("cuda", 0)
+    hits = np.ascontiguousarray(g["hits"]).astype(np.int32)
+    T, K = hits.shape
+    xyz, lcov, lay = f32(stress["xyz"].T, dev), f32(stress["lcov"].T, dev), i32(stress["lay"], dev)
+    hd = i32(hits, dev)
+    ckpt = torch.empty((K, 27, T), dtype=torch.float32, device=dev)
+    fo = mkf.mkf_fit_tracks(ctx, xyz, lcov, lay, hd, f32(stress["sp"].T, dev), f32(stress["sc"].T, dev), ckpt=ckpt)
+    mkf.mkf_sync(ctx)
+    nh = (hits >= 0).sum(1)
+    rng = np.random.default_rng(22)
+    pick = np.sort(rng.choice(np.nonzero(nh >= 4)[0], 200, replace=False))
+    geo = oracle.Geo.of(b.geom)
+    fpar, fcov, fchi, fok = oracle.fit(geo, stress["xyz"], stress["lcov"], stress["lay"], hits[pick],
+                                       stress["sp"][pick], stress["sc"][pick])
+    gp = fo["par"].cpu().numpy().T.astype(np.float64)[pick]
+    gc = fo["cov"].cpu().numpy().T.astype(np.float64)[pick]
+    gx = fo["chi2"].cpu().numpy().astype(np.float64)[pick]
+    good = fok.astype(bool) & (fo["ok"].cpu().numpy()[pick] == 1)
+    assert good.mean() > 0.95
+    pe, ce = par_rel_err(gp[good], fpar[good]), cov_rel_err(gc[good], fcov[good])
+    xe = np.abs(gx[good] - fchi[good]) / np.maximum(fchi[good], 1.0)
+    print("C5 outward refit: %d tracks, par err" % good.sum(), pe.max(0), "cov err", ce.max(), "chi2 err", xe.max())
+    assert pe.max() < PAR_RTOL
+    assert ce.max() < COV_RTOL
+    assert xe.max() < CHI2_RTOL
+    # inward fit of every track; the sampled ones start from the oracle's outward state
+    q = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    init = fo["par"].clone()
+    fq = q(fpar)
+    init[:, torch.as_tensor(pick, device=dev)] = f32(fq.T, dev)
+    bo = mkf.mkf_fit_backward(ctx, xyz, lcov, lay, hd, init)
+    mkf.mkf_sync(ctx)
+    bpar, bcov, _, bok = oracle.fit(geo, stress["xyz"], stress["lcov"], stress["lay"], hits[pick], fq, fcov,
+                                    direction=-1)
+    gbp = bo["par"].cpu().numpy().T.astype(np.float64)[pick]
+    gbc = bo["cov"].cpu().numpy().T.astype(np.float64)[pick]
+    good = good & bok.astype(bool) & (bo["ok"].cpu().numpy()[pick] == 1)
+    pe, ce = par_rel_err(gbp[good], bpar[good]), cov_rel_err(gbc[good], bcov[good])
+    print("C5 inward refit: %d tracks, par err" % good.sum(), pe.max(0), "cov err", ce.max())
+    assert pe.max() < PAR_RTOL
+    assert ce.max() < COV_RTOL
