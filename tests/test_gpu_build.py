@@ -92,10 +92,17 @@ def test_build_config1_full_event(max_cands):
 
 def test_build_config2_sampled_seeds():
     """CMS-like 38-surface event at full size (5000 tracks, 85k hits incl. 20 %
-    noise) on the GPU; the oracle builds a sample of 500 seeds against the full
-    hit set and every sampled seed is compared."""
+    noise) on the GPU, in the binning and launch shape the autotuner picks (as
+    the benchmark does); the oracle builds a sample of 500 seeds against the
+    full hit set and every sampled seed is compared."""
+    from paper_2002_06295_gb300 import tune
     ev = synth.make_config_event(2)
     ctx = make_ctx(ev.geom)
+    dev = torch.device("cuda", 0)
+    tuned = tune.autotune_build(ctx, ev.geom.table(), ev.geom.bz, f32(ev.hit_xyz.T, dev), f32(ev.hit_lcov.T, dev),
+                                i32(ev.hit_layer, dev), i64([0, ev.n_hits], dev), f32(ev.seed_par.T, dev),
+                                f32(ev.seed_cov.T, dev), i64([0, ev.n_seeds], dev), max_cands=6)
+    print("C2 launch:", tuned)
     g = gpu_build(ctx, [ev], max_cands=6)
     sel = np.random.default_rng(7).choice(ev.n_seeds, 500, replace=False)
     r = oracle_build([ev], max_cands=6, seeds=sel, dedup=False)
