@@ -348,23 +348,9 @@ def measure_in_flight(mkf, dev, counts=(1, 2, 4), rounds=20):
         g_chi2 = torch.ones(S, device=dev)
         adj = dict(g_hit=torch.empty((3, ev.n_hits), device=dev), g_align=torch.empty((L, 3), device=dev),
                    g_x0=torch.empty(L, device=dev))
-        main, side = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
-        fwd_done, bwd_done = torch.cuda.Event(), torch.cuda.Event()
-
-        def step():
-            mkf.mkf_bin_hits(ctx, d["xyz"], d["lcov"], d["layer"], d["hoff"])
-            mkf.mkf_build_tracks(ctx, d["sp"], d["sc"], d["soff"], out=out, **kw)
-            mkf.mkf_fit_tracks(ctx, d["xyz"], d["lcov"], d["layer"], out["hits"], d["sp"], d["sc"], ckpt=ckpt,
-                               out=fit_out)
-            cur = torch.cuda.current_stream()
-            fwd_done.record(cur)
-            side.wait_event(fwd_done)
-            mkf.mkf_fit_backward(ctx, d["xyz"], d["lcov"], d["layer"], out["hits"], fit_out["par"], out=bwd_out,
-                                 stream=side)
-            bwd_done.record(side)
-            mkf.mkf_fit_tracks_adjoint(ctx, d["xyz"], d["lcov"], d["layer"], out["hits"], d["sp"], d["sc"], ckpt,
-                                       g_chi2=g_chi2, out=adj)
-            cur.wait_event(bwd_done)
+        main = torch.cuda.Stream(device=dev)
+        step_d = make_step(mkf, ctx, kw, ev.n_hits, out, ckpt, fit_out, bwd_out, adj, g_chi2)
+        step = lambda: step_d(d)
 
         with torch.cuda.stream(main):
             for _ in range(3):
@@ -377,7 +363,7 @@ def measure_in_flight(mkf, dev, counts=(1, 2, 4), rounds=20):
             with torch.cuda.graph(cg, stream=main):
                 step()
         torch.cuda.synchronize()
-        return dict(ctx=ctx, graph=cg, stream=main, units=units, keep=(d, out, ckpt, fit_out, bwd_out, adj, side))
+        return dict(ctx=ctx, graph=cg, stream=main, units=units, keep=(d, out, ckpt, fit_out, bwd_out, adj, step_d))
 
     items = [make(e) for e in range(max(counts))]
     flush = torch.empty(256 * 1024 * 1024 // 4, device=dev)   # > 129 MB L2
@@ -690,7 +676,7 @@ def measure_overlaps(mkf, dev, reps=5):
 
 
 KERNEL_SOURCES = ("paper_2002_06295_gb300/csrc/build.cu", "paper_2002_06295_gb300/csrc/mkf_device.cuh",
-                  "paper_2002_06295_gb300/csrc/mkf_geom.h")
+                  "paper_2002_06295_gb300/csrc/mkf_ud.cuh", "paper_2002_06295_gb300/csrc/mkf_geom.h")
 STRIP_SOURCES = ("paper_2002_06295_gb300/csrc/strips.cu", "paper_2002_06295_gb300/csrc/mkf_geom.h")
 SEED_SOURCES = ("paper_2002_06295_gb300/csrc/seeds.cu", "paper_2002_06295_gb300/csrc/mkf_device.cuh",
                 "paper_2002_06295_gb300/csrc/mkf_geom.h")
@@ -791,6 +777,43 @@ def gather_results(dist, local):
     return out
 
 
+def make_step(mkf, ctx, kw, n_hits, out, ckpt, fit_out, bwd_out, adj_out, g_chi2):
+    """One step of the path as stream-ordered library calls, capturable as one
+    CUDA graph: binning -> building -> forward fit with checkpoints -> adjoint
+    on the current stream; duplicate removal on a second stream beside the
+    fits (it writes only the flags, which no fit reads) and the inward fit on a
+    third once the forward fit is done; the current stream waits for both.
+    Duplicate removal is switched out of mkf_build_tracks on this context."""
+    import torch
+    dev = torch.device("cuda", ctx.device)
+    mkf.mkf_set_build_dedup(ctx, False)
+    dd_side, bwd_side = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    built, dd_done, fwd_done, bwd_done = (torch.cuda.Event() for _ in range(4))
+
+    def step(inp):
+        cur = torch.cuda.current_stream()
+        mkf.mkf_bin_hits(ctx, inp["xyz"], inp["lcov"], inp["layer"], inp["hoff"])
+        mkf.mkf_build_tracks(ctx, inp["sp"], inp["sc"], inp["soff"], out=out, **kw)
+        built.record(cur)
+        dd_side.wait_event(built)
+        mkf.mkf_dedup_tracks(ctx, out["hits"], out["score"], out["counts"][0], inp["soff"], n_hits,
+                             min_hits=kw["min_hits"], dup_frac=kw["dup_frac"], out_flags=out["flags"], stream=dd_side)
+        dd_done.record(dd_side)
+        mkf.mkf_fit_tracks(ctx, inp["xyz"], inp["lcov"], inp["layer"], out["hits"], inp["sp"], inp["sc"],
+                           ckpt=ckpt, out=fit_out)
+        fwd_done.record(cur)
+        bwd_side.wait_event(fwd_done)
+        mkf.mkf_fit_backward(ctx, inp["xyz"], inp["lcov"], inp["layer"], out["hits"], fit_out["par"], out=bwd_out,
+                             stream=bwd_side)
+        bwd_done.record(bwd_side)
+        mkf.mkf_fit_tracks_adjoint(ctx, inp["xyz"], inp["lcov"], inp["layer"], out["hits"], inp["sp"], inp["sc"],
+                                   ckpt, g_chi2=g_chi2, out=adj_out)
+        cur.wait_event(bwd_done)
+        cur.wait_event(dd_done)
+
+    return step
+
+
 def time_path(mkf, dev, evs, spec, steps, warmup, dist=None, clocks=None, graph=True):
     """Time the whole path on one batch of events: binning -> building with
     duplicate removal -> forward fit with checkpoints -> adjoint, beside the
@@ -831,25 +854,8 @@ def time_path(mkf, dev, evs, spec, steps, warmup, dist=None, clocks=None, graph=
                    g_x0=torch.empty(L, device=dev))
     stream = torch.cuda.current_stream()
     mkf.mkf_set_timing(ctx, True)
-    side = torch.cuda.Stream(device=dev)      # the inward fit runs beside the adjoint
-    fwd_done, bwd_done = torch.cuda.Event(), torch.cuda.Event()
-
-    def step(inp):
-        mkf.mkf_bin_hits(ctx, inp["xyz"], inp["lcov"], inp["layer"], inp["hoff"])
-        mkf.mkf_build_tracks(ctx, inp["sp"], inp["sc"], inp["soff"], chi2_cut=spec["chi2_cut"],
-                             max_cands=spec["max_cands"], max_holes=spec["max_holes"], min_hits=spec["min_hits"],
-                             dup_frac=spec["dup_frac"], out=out)
-        mkf.mkf_fit_tracks(ctx, inp["xyz"], inp["lcov"], inp["layer"], out["hits"], inp["sp"], inp["sc"],
-                           ckpt=ckpt, out=fit_out)
-        cur = torch.cuda.current_stream()
-        fwd_done.record(cur)
-        side.wait_event(fwd_done)
-        mkf.mkf_fit_backward(ctx, inp["xyz"], inp["lcov"], inp["layer"], out["hits"], fit_out["par"], out=bwd_out,
-                             stream=side)
-        bwd_done.record(side)
-        mkf.mkf_fit_tracks_adjoint(ctx, inp["xyz"], inp["lcov"], inp["layer"], out["hits"], inp["sp"], inp["sc"],
-                                   ckpt, g_chi2=g_chi2, out=adj_out)
-        cur.wait_event(bwd_done)
+    kw = {k: spec[k] for k in ("chi2_cut", "max_cands", "max_holes", "min_hits", "dup_frac")}
+    step = make_step(mkf, ctx, kw, n_hits, out, ckpt, fit_out, bwd_out, adj_out, g_chi2)
 
     dd_inputs = {k: torch.empty_like(v) for k, v in d.items()}   # device copies of the host inputs (e2e)
     for k, v in d.items():

@@ -276,6 +276,16 @@ mkf_status mkf_build_tracks(mkf_ctx* ctx, const float* seed_par, const float* se
  * (paper_2002_06295_gb300/tune.py); it changes speed only, never results. */
 mkf_status mkf_set_build_config(mkf_ctx* ctx, int warps_per_block, int lanes_per_seed);
 
+/* Duplicate removal inside mkf_build_tracks (abstract: an additional
+ * processing step after building).  enabled = 1 (default): mkf_build_tracks
+ * ends with it and writes out_flags.  enabled = 0: mkf_build_tracks leaves
+ * out_flags of the built seeds unwritten (rows past ev_seed_off[E] are still
+ * written MKF_TRK_SHORT), and the caller runs mkf_dedup_tracks on the built
+ * tracks (nhits = out_counts[0]), which gives the same flags.  Because the fits
+ * do not read the flags, that call may then run on another stream beside
+ * mkf_fit_tracks.  MKF_ERR_ARG unless 0 or 1. */
+mkf_status mkf_set_build_dedup(mkf_ctx* ctx, int enabled);
+
 /* Work split of mkf_cluster_strips (TMA path): strips per staged chunk,
  * events per work item (an item is 32 consecutive modules of that many events,
  * whose calibration is staged once per chunk) and pipeline stages per warp.

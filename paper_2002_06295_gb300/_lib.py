@@ -28,6 +28,7 @@ SIGNATURES = {
     "mkf_set_debug": (i32, [P, i32]),
     "mkf_set_build_config": (i32, [P, i32, i32]),
     "mkf_set_adjoint_config": (i32, [P, i32]),
+    "mkf_set_build_dedup": (i32, [P, i32]),
     "mkf_get_stats": (i32, [P, P, i32, P]),
     "mkf_set_timing": (i32, [P, i32]),
     "mkf_get_timings": (i32, [P, P, i32, P]),

@@ -165,6 +165,10 @@ def mkf_set_build_config(ctx, warps_per_block=4, lanes_per_seed=0):
     ctx._check(ctx.lib.mkf_set_build_config(ctx.h, int(warps_per_block), int(lanes_per_seed)), "mkf_set_build_config")
 
 
+def mkf_set_build_dedup(ctx, enabled=True):
+    ctx._check(ctx.lib.mkf_set_build_dedup(ctx.h, int(enabled)), "mkf_set_build_dedup")
+
+
 def mkf_set_adjoint_config(ctx, lanes_per_track=0):
     ctx._check(ctx.lib.mkf_set_adjoint_config(ctx.h, int(lanes_per_track)), "mkf_set_adjoint_config")
 

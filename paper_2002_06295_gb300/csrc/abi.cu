@@ -227,6 +227,13 @@ mkf_status mkf_set_build_config(mkf_ctx* ctx, int warps_per_block, int lanes_per
   return MKF_OK;
 }
 
+mkf_status mkf_set_build_dedup(mkf_ctx* ctx, int enabled) {
+  if (check_ctx(ctx)) return MKF_ERR_ARG;
+  if (enabled != 0 && enabled != 1) return ctx->fail(MKF_ERR_ARG, "enabled must be 0 or 1");
+  ctx->build_dedup = enabled;
+  return MKF_OK;
+}
+
 mkf_status mkf_set_adjoint_config(mkf_ctx* ctx, int lanes_per_track) {
   if (check_ctx(ctx)) return MKF_ERR_ARG;
   if (lanes_per_track != 0 && lanes_per_track != 1 && lanes_per_track != 8)

@@ -104,15 +104,43 @@ __device__ __forceinline__ uint64_t child_key(float score, int slot, uint32_t hi
   return ((uint64_t)(~ordered(score)) << 32) | ((uint64_t)slot << 28) | hitkey;
 }
 
+// Plain (volatile) read of the NMAX slots of a seed's top-N array; the array
+// starts on a 16-byte boundary when NMAX >= 2.
+template <int NMAX>
+__device__ __forceinline__ void top_read(const unsigned long long* ts, unsigned long long (&v)[NMAX]) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(ts);
+  if constexpr (NMAX == 1) {
+    asm volatile("ld.volatile.shared.u64 %0, [%1];\n" : "=l"(v[0]) : "r"(a) : "memory");
+  } else {
+#pragma unroll
+    for (int j = 0; j < NMAX; j += 2)
+      asm volatile("ld.volatile.shared.v2.u64 {%0, %1}, [%2];\n" : "=l"(v[j]), "=l"(v[j + 1]) : "r"(a + 8 * j) : "memory");
+  }
+}
+
 // Insert key k into the ascending array ts[0..n) that holds the n smallest
 // keys inserted so far (~0 = empty).  Any number of lanes may insert
 // concurrently: every key reaching slot j leaves the smaller of it and the
 // slot's value there and carries the larger on, so slot j ends up holding the
 // j-th smallest key whatever the interleaving.  Slot values only decrease, so
-// a key not below the current last slot can never enter and is dropped at once.
+// a slot read at or below the carried key stays there, and its atomicMin
+// would change nothing: such slots are skipped on the strength of one plain
+// read of the array, and the cascade of atomics starts at the first slot read
+// above the key (a key not below the last slot can never enter and is
+// dropped at once).  The result is the same as with an atomic on every slot.
+template <int NMAX>
 __device__ __forceinline__ void top_insert(unsigned long long* ts, int n, unsigned long long k) {
-  if (!(k < *reinterpret_cast<volatile unsigned long long*>(&ts[n - 1]))) return;
-  for (int j = 0; j < n; ++j) {
+  unsigned long long v[NMAX];
+  top_read<NMAX>(ts, v);
+  unsigned long long last = v[0];
+#pragma unroll
+  for (int j = 1; j < NMAX; ++j)
+    if (j == n - 1) last = v[j];
+  if (!(k < last)) return;
+#pragma unroll
+  for (int j = 0; j < NMAX; ++j) {
+    if (j >= n) break;
+    if (v[j] <= k) continue;
     const unsigned long long old = atomicMin(&ts[j], k);
     if (old == ~0ull) return;
     k = old > k ? old : k;
@@ -180,8 +208,12 @@ __device__ __forceinline__ uint64_t group_max(uint64_t v, unsigned gm) {
   return ((uint64_t)mh << 32) | ml;
 }
 
-template <int NMAX, bool DEBUG>
-__global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
+// MINB = 2 caps the registers at 128 per thread so that two 8-warp blocks fit
+// an SM (the batched workloads, whose shared footprint allows two); MINB = 1
+// lets the compiler keep the whole per-step working set in registers (no
+// spills) where shared memory admits only one block per SM anyway.
+template <int NMAX, bool DEBUG, int MINB>
+__global__ void __launch_bounds__(kMaxWarps * 32, MINB) k_build(const BuildDev a) {
   extern __shared__ __align__(16) unsigned char smem[];
   GeomDev& G = *reinterpret_cast<GeomDev*>(smem);
   // shared scan jobs, one per warp: next = epoch << 16 | rounds claimed
@@ -326,7 +358,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
       if (chi2 < cut) {
         cnt[ow * 32 + cc] = 1;   // the candidate has a child (only "none" is tested)
         const uint32_t hloc = (uint32_t)(hr.orig - wd[10]);
-        top_insert(top + (ow * NG + cc / GS) * NMAX, N,
+        top_insert<NMAX>(top + (ow * NG + cc / GS) * NMAX, N,
                    child_key(ps[27] + 10.0f - chi2, cc & (GS - 1), hloc < kHoleKey ? hloc : kHoleKey - 1));
       }
     }
@@ -386,10 +418,27 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
       cot_t = cos_t / sin_t;
       omega = ck * p[3];
       msincos(p[4], &sph, &cph);
+      // The transverse path to radius R is at least R - r0 (an arc is no
+      // shorter than its chord), and z moves monotonically along it, so a
+      // barrel whose z range lies behind z0 + (R - r0) cot(theta) on the side
+      // of motion cannot be crossed inside its acceptance.  The path bound is
+      // shrunk by a margin far above FP32 rounding, so this test rejects only
+      // barrels that the exact crossing would reject too; it is armed once a
+      // crossing has fallen outside a barrel's z range (forward tracks), so
+      // that tracks accepted by their first barrel pay nothing for it.
+      bool zcut = false;
+      float r0 = 0.f;
       // surfaces already passed form a prefix of each sorted list
       for (int i = first_above(G.barrel_r, G.n_barrel, rho + kNavEps); i < G.n_barrel; ++i) {
         const int l = G.barrel_order[i];
         const LayerDev& ly = G.L[l];
+        if (zcut) {
+          const float smin = fmaf(ly.pos - r0, 0.999f, -1e-3f);
+          if (smin > 0.0f) {
+            const float zb = fmaf(smin, cot_t, p[2]);
+            if (cot_t > 0.0f ? zb > ly.hi : zb < ly.lo) continue;
+          }
+        }
         ++n_nav;
         const float s = cylinder_path(p[0], p[1], cph, sph, omega, ly.pos, +1);
         if (!(s < INFINITY)) break;    // the particle's circle stays inside: larger radii too
@@ -398,6 +447,10 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
           nl = l;
           ns = s;
           break;
+        }
+        if (!zcut) {
+          zcut = true;
+          r0 = sqrtf(fmaf(p[0], p[0], p[1] * p[1]));
         }
       }
       if (cot_t != 0.0f) {
@@ -661,7 +714,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_build(const BuildDev a) {
         }
       }
     }
-    if (hole_ok) top_insert(gtop, N, child_key(score - 10.0f, li, kHoleKey));
+    if (hole_ok) top_insert<NMAX>(gtop, N, child_key(score - 10.0f, li, kHoleKey));
     __syncwarp();
     const int nk = nl >= 0 ? cnt[warp * 32 + lane] + (hole_ok ? 1 : 0) : 0;
     const bool finishing = active && (nl < 0 || nk == 0);
@@ -833,27 +886,47 @@ size_t build_smem(int L, int W, int GS) {
          (size_t)W * NG * L * NMAX * 4;
 }
 
-template <int NMAX, bool DEBUG>
-cudaError_t run_build(mkf_ctx* ctx, const BuildDev& d, cudaStream_t st) {
-  int W = ctx->build_warps;
-  if (W < 1 || W > kMaxWarps) W = 4;
+template <int NMAX, bool DEBUG, int MINB>
+cudaError_t launch_build_kernel(mkf_ctx* ctx, const BuildDev& d, int W, size_t sm, int per_sm, cudaStream_t st) {
   const int GS = d.gsize;
-  const size_t sm = build_smem<NMAX>(ctx->geom.n_layers, W, GS);
-  cudaError_t e = cudaFuncSetAttribute(k_build<NMAX, DEBUG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build<NMAX, DEBUG>, W * 32, sm);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
   const int64_t groups_needed = (d.n_seeds + (32 / GS) - 1) / (32 / GS);
   const int64_t blocks = (groups_needed + W - 1) / W;
   int64_t grid = (int64_t)ctx->n_sm * per_sm;
   if (blocks < grid) grid = blocks;
   if (grid < 1) grid = 1;
   ctx->tick(kTBuild, st);
-  k_build<NMAX, DEBUG><<<(unsigned)grid, W * 32, sm, st>>>(d);
+  k_build<NMAX, DEBUG, MINB><<<(unsigned)grid, W * 32, sm, st>>>(d);
   ctx->tock(kTBuild, st);
   return cudaGetLastError();
+}
+
+// Blocks of the kernel instance that fit one SM with this launch's shared memory.
+template <int NMAX, bool DEBUG, int MINB>
+cudaError_t build_occupancy(int W, size_t sm, int* per_sm) {
+  cudaError_t e =
+      cudaFuncSetAttribute(k_build<NMAX, DEBUG, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  *per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_build<NMAX, DEBUG, MINB>, W * 32, sm);
+  if (*per_sm < 1) *per_sm = 1;
+  return e;
+}
+
+// The register-unbounded instance (MINB = 1) is launched when it keeps as many
+// blocks per SM as the 128-register one; otherwise the 128-register instance.
+template <int NMAX, bool DEBUG>
+cudaError_t run_build(mkf_ctx* ctx, const BuildDev& d, cudaStream_t st) {
+  int W = ctx->build_warps;
+  if (W < 1 || W > kMaxWarps) W = 4;
+  const size_t sm = build_smem<NMAX>(ctx->geom.n_layers, W, d.gsize);
+  int per2 = 0, per1 = 0;
+  cudaError_t e = build_occupancy<NMAX, DEBUG, 2>(W, sm, &per2);
+  if (e != cudaSuccess) return e;
+  if constexpr (!DEBUG) {
+    if ((e = build_occupancy<NMAX, DEBUG, 1>(W, sm, &per1)) != cudaSuccess) return e;
+    if (per1 >= per2) return launch_build_kernel<NMAX, DEBUG, 1>(ctx, d, W, sm, per1, st);
+  }
+  return launch_build_kernel<NMAX, DEBUG, 2>(ctx, d, W, sm, per2, st);
 }
 
 }  // namespace
@@ -912,6 +985,7 @@ cudaError_t launch_build(mkf_ctx* ctx, const BuildArgs& a, cudaStream_t st) {
       e = run_build<8, false>(ctx, d, st);
     if (e != cudaSuccess) return e;
   }
+  if (!ctx->build_dedup) return cudaSuccess;   // the caller runs mkf_dedup_tracks
   return launch_dedup(ctx, a.out_hits, ctx->geom.n_layers, a.out_score, ctx->track_hits.as<int>(), a.ev_seed_off,
                       ctx->n_events, S, ctx->n_hits, a.min_hits, a.dup_frac, a.out_flags, st);
 }

@@ -346,3 +346,43 @@ def test_batched_full_size_sampled_seeds():
     print("C3 full size, sampled seeds:", rep_total)
     assert rep_total["fragile"] <= 0.2 * rep_total["n"]
     ctx.close()
+
+
+def test_dedup_split_from_building_on_a_side_stream():
+    """With duplicate removal switched off in mkf_build_tracks, the flags are
+    left to mkf_dedup_tracks; run on a second stream beside the outward fit,
+    it gives the flags of the combined call bit for bit, and nothing else of
+    the building output changes."""
+    import paper_2002_06295_gb300 as mkf
+    dev = torch.device("cuda", 0)
+    evs = [synth.make_config_event(3, e, n_tracks=n) for e, n in enumerate([400, 30, 900])]
+    ref = gpu_build(make_ctx(evs[0].geom), evs, max_cands=4)
+    ctx = make_ctx(evs[0].geom)
+    with pytest.raises(mkf.MkfError):
+        mkf.mkf_set_build_dedup(ctx, 2)
+    mkf.mkf_set_build_dedup(ctx, False)
+    cat = lambda name: np.concatenate([getattr(e, name) for e in evs], 0)
+    xyz, lcov, lay = f32(cat("hit_xyz").T, dev), f32(cat("hit_lcov").T, dev), i32(cat("hit_layer"), dev)
+    sp, sc = f32(cat("seed_par").T, dev), f32(cat("seed_cov").T, dev)
+    soff = i64(ref["seed_off"], dev)
+    mkf.mkf_bin_hits(ctx, xyz, lcov, lay, i64(ref["hit_off"], dev))
+    S = int(ref["seed_off"][-1])
+    out = mkf.alloc_build_outputs(ctx, S)
+    out["flags"].fill_(-7)
+    mkf.mkf_build_tracks(ctx, sp, sc, soff, max_cands=4, out=out)
+    mkf.mkf_sync(ctx)
+    assert (out["flags"] == -7).all()          # left to mkf_dedup_tracks
+    side = torch.cuda.Stream(device=dev)
+    built = torch.cuda.Event()
+    built.record(torch.cuda.current_stream())
+    side.wait_event(built)
+    flags = torch.full((S,), -7, dtype=torch.int32, device=dev)
+    mkf.mkf_dedup_tracks(ctx, out["hits"], out["score"], out["counts"][0], soff, int(ref["hit_off"][-1]),
+                         min_hits=4, dup_frac=0.5, out_flags=flags, stream=side)
+    mkf.mkf_fit_tracks(ctx, xyz, lcov, lay, out["hits"], sp, sc)
+    torch.cuda.synchronize()
+    mkf.mkf_sync(ctx)
+    assert np.array_equal(flags.cpu().numpy(), ref["flags"])
+    for k in ("hits", "layers", "counts", "score"):
+        assert np.array_equal(out[k].cpu().numpy(), ref[k]), k
+    ctx.close()
