@@ -968,9 +968,9 @@ def time_path(mkf, dev, evs, spec, steps, warmup, dist=None, clocks=None, graph=
                 clocks=clk)
 
 
-# kernels of one step: binning 5 (keys, 3-pass scan, scatter), building 1,
-# dedup 3, forward fit 1, adjoint 1, inward fit 1
-LAUNCHES_PER_STEP = 5 + 1 + 3 + 1 + 1 + 1
+# kernels of one step: binning 5 (keys, 3-pass scan, scatter), building 2
+# (seed order, build), dedup 3, forward fit 1, adjoint 1, inward fit 1
+LAUNCHES_PER_STEP = 5 + 2 + 3 + 1 + 1 + 1
 
 
 def path_summary(r, workload, dev, max_mhz=None):

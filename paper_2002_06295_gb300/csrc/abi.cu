@@ -57,7 +57,7 @@ void mkf_destroy(mkf_ctx* ctx) {
   DevBuf* bufs[] = {&ctx->geom_dev, &ctx->rec,     &ctx->rec_orig,  &ctx->perm,     &ctx->bin_off,
                     &ctx->bin_cnt,  &ctx->keys,    &ctx->ranks,     &ctx->vmax,     &ctx->ev_hit_off,
                     &ctx->scan_part, &ctx->seed_ctr, &ctx->stats,    &ctx->status,   &ctx->dd_head,
-                    &ctx->dd_next,  &ctx->dd_beat, &ctx->dd_nbeat,  &ctx->dd_state, &ctx->track_hits,
+                    &ctx->dd_next,  &ctx->dd_beat, &ctx->dd_nbeat,  &ctx->dd_state, &ctx->track_hits, &ctx->build_order,
                     &ctx->strip_bits, &ctx->seed_cnt, &ctx->seed_off, &ctx->seed_part, &ctx->seed_pairs,
                     &ctx->seed_qcnt, &ctx->seed_qoff, &ctx->grid_key, &ctx->grid_rank, &ctx->grid_cnt,
                     &ctx->grid_off, &ctx->grid_rec, &ctx->seed_stats, &ctx->ovl_stats,

@@ -30,6 +30,9 @@
 //    predicted chi2), reading the parent's propagated state from shared memory;
 //  * groups take seeds from a global queue (atomic counter) and refill as soon
 //    as their seed is done, so one launch covers many events of uneven size;
+//    the queue holds each event's seeds most expensive first (by 1/p), and
+//    its first places are dealt so that those seeds spread one to a warp over
+//    all blocks;
 //    a warp without seeds helps the other warps of its block scan their wide
 //    windows (shared-memory jobs claimed by CAS, every wait bounded);
 //  * the parent pointers and hits of every step stay in shared memory and are
@@ -70,6 +73,7 @@ struct BuildDev {
   const float* seed_par;
   const float* seed_cov;
   const int64_t* ev_seed_off;
+  const int* order;   // building order of the seed rows (k_seed_order)
   int64_t n_seeds;
   int n_events;
   float chi2_cut;
@@ -311,12 +315,32 @@ __global__ void __launch_bounds__(kMaxWarps * 32, MINB) k_build(const BuildDev a
 
   // Take the next seed for every group with want == true.  Called by all lanes
   // of the warp together (it shuffles).
+  // The first seeds are dealt, not queued: group g of warp w in block b takes
+  // place (g W + w) gridDim + b of the building order, so the most expensive
+  // seeds of an event (the order puts them first) go one to a warp and spread
+  // over all blocks, instead of landing wherever the queue's first atomics
+  // happen to come from; every later seed comes from the queue.
+  const int64_t n_dealt = (int64_t)gridDim.x * W * NG;
+  bool first = true;
   auto fetch = [&](bool want) {
     unsigned long long s = 0;
-    if (want && li == 0) s = atomicAdd(a.seed_ctr, 1ull);
+    if (want && li == 0) {
+      if (first)
+        s = ((unsigned long long)gi * W + warp) * gridDim.x + blockIdx.x;
+      else
+        s = (unsigned long long)n_dealt + atomicAdd(a.seed_ctr, 1ull);
+    }
+    first = false;
     s = __shfl_sync(0xffffffffu, s, gbase);
     if (!want) return;
-    seed = (int64_t)s < n_run ? (int64_t)s : -1;
+    if ((int64_t)s < n_run) {
+      // order[] holds every row below n_run once when the event offsets are
+      // consistent; anything else read there is replaced by the plain row
+      const int o = a.order[s];
+      seed = o >= 0 && (int64_t)o < n_run ? (int64_t)o : (int64_t)s;
+    } else {
+      seed = -1;
+    }
     active = false;
     step = 0;
     if (seed >= 0) {
@@ -877,6 +901,49 @@ __global__ void __launch_bounds__(kMaxWarps * 32, MINB) k_build(const BuildDev a
   }
 }
 
+// Building order of the seed rows: within each event (whose rows stay in
+// their range, events in order) the seeds by descending expected cost, taken
+// as sin(theta) |kappa| = 1/p of the seed: slow particles curl and scatter,
+// so their windows are wide and their chains of steps long.  The order only
+// decides when a seed is built; the tracks do not depend on it.  One block per
+// event: a 64-bucket counting sort on log2(1/p) (quarter octaves), rows of one
+// bucket in any order.
+constexpr int kOrderBuckets = 64;
+// Rows before the first offset count with event 0 (as in the building kernel's
+// event lookup); offsets are clamped to the rows that are built.
+__global__ void k_seed_order(const float* __restrict__ seed_par, const int64_t* __restrict__ ev_seed_off,
+                             int n_events, int64_t n_seeds, int* __restrict__ order) {
+  __shared__ int cnt[kOrderBuckets];
+  int64_t n_run = ev_seed_off[n_events];
+  n_run = n_run < 0 ? 0 : (n_run < n_seeds ? n_run : n_seeds);
+  const int e = blockIdx.x;
+  int64_t s0 = e == 0 ? 0 : ev_seed_off[e];
+  int64_t s1 = ev_seed_off[e + 1];
+  s0 = s0 < 0 ? 0 : (s0 < n_run ? s0 : n_run);
+  s1 = s1 < s0 ? s0 : (s1 < n_run ? s1 : n_run);
+  if (threadIdx.x < kOrderBuckets) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  auto bucket = [&](int64_t r) {
+    const float ip = fabsf(seed_par[3 * n_seeds + r]) * fabsf(sinf(seed_par[5 * n_seeds + r]));
+    // 1/p from 2^-4 to 2^12 /GeV in quarter octaves; heavy (large 1/p) first
+    const float q = 4.0f * (log2f(fmaxf(ip, 1e-30f)) + 4.0f);
+    const int b = (int)fminf(fmaxf(q, 0.0f), (float)(kOrderBuckets - 1));
+    return kOrderBuckets - 1 - b;
+  };
+  for (int64_t r = s0 + threadIdx.x; r < s1; r += blockDim.x) atomicAdd(&cnt[bucket(r)], 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int b = 0; b < kOrderBuckets; ++b) {
+      const int c = cnt[b];
+      cnt[b] = acc;
+      acc += c;
+    }
+  }
+  __syncthreads();
+  for (int64_t r = s0 + threadIdx.x; r < s1; r += blockDim.x) order[s0 + atomicAdd(&cnt[bucket(r)], 1)] = (int)r;
+}
+
 template <int NMAX>
 size_t build_smem(int L, int W, int GS) {
   const int NG = 32 / GS;
@@ -935,6 +1002,7 @@ cudaError_t launch_build(mkf_ctx* ctx, const BuildArgs& a, cudaStream_t st) {
   cudaError_t e;
   const int64_t S = a.n_seeds;
   if ((e = ctx->track_hits.ensure((size_t)(S > 0 ? S : 1) * 4)) != cudaSuccess) return e;
+  if ((e = ctx->build_order.ensure((size_t)(S > 0 ? S : 1) * 4)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(ctx->seed_ctr.p, 0, sizeof(unsigned long long), st))) return e;
   if ((e = cudaMemsetAsync(ctx->stats.p, 0, 8 * sizeof(int64_t), st))) return e;
   if (S > 0) {
@@ -948,6 +1016,7 @@ cudaError_t launch_build(mkf_ctx* ctx, const BuildArgs& a, cudaStream_t st) {
     d.seed_par = a.seed_par;
     d.seed_cov = a.seed_cov;
     d.ev_seed_off = a.ev_seed_off;
+    d.order = ctx->build_order.as<int>();
     d.n_seeds = S;
     d.n_events = ctx->n_events;
     d.chi2_cut = a.chi2_cut;
@@ -971,6 +1040,9 @@ cudaError_t launch_build(mkf_ctx* ctx, const BuildArgs& a, cudaStream_t st) {
     d.seed_ctr = ctx->seed_ctr.as<unsigned long long>();
     d.stats = ctx->stats.as<unsigned long long>();
     d.status = ctx->status.as<int>();
+    if (ctx->n_events > 0)
+      k_seed_order<<<(unsigned)ctx->n_events, 256, 0, st>>>(a.seed_par, a.ev_seed_off, ctx->n_events, S,
+                                                            ctx->build_order.as<int>());
     // the brute-force window check has a kernel of its own (any N <= 8), so
     // the production kernels carry none of its code
     if (d.debug)

@@ -83,6 +83,7 @@ struct mkf_ctx {
 
   // build / dedup
   mkf::DevBuf seed_ctr, stats, status, dd_head, dd_next, dd_beat, dd_nbeat, dd_state, track_hits;
+  mkf::DevBuf build_order;  // seeds in building order (per event, expected cost descending)
   mkf::DevBuf strip_bits;  // bad-strip flags packed to bits for the clustering kernel
   mkf::DevBuf seed_cnt, seed_off, seed_part, seed_pairs, seed_qcnt, seed_qoff;   // hit-based seeding
   mkf::DevBuf grid_key, grid_rank, grid_cnt, grid_off, grid_rec;                // its search grid
