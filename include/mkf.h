@@ -372,7 +372,12 @@ mkf_status mkf_dedup_tracks_noalloc(const int* hits, int L, const float* score, 
  *                         hit radii by dr, azimuths by dphi
  *   x0 [L] or NULL        per-layer thickness overriding the geometry's
  * Outputs: out_par [6][T], out_cov [21][T], out_chi2 [T] (sum of chi2),
- *   out_ok [T] or NULL (1: every surface reached),
+ *   out_ok [T] or NULL: 1 every surface reached; 2 every surface reached, and
+ *     a transport onto an endcap disk spans a full turn of the helix or more
+ *     (|s omega| >= 2 pi: a slow particle near theta = pi/2 drifting from disk
+ *     to disk over several turns), on which mkf_fit_tracks_adjoint's FP32
+ *     reverse sweep is not accurate, so it leaves the track out; 0 a surface
+ *     not reached,
  *   ckpt [K][27][T] or NULL: state (6 parameters, 21 covariance) before step k,
  *   needed by mkf_fit_tracks_adjoint. */
 mkf_status mkf_fit_tracks(mkf_ctx* ctx, const float* xyz, const float* lcov, const int* layer, int64_t n_hits,
@@ -402,7 +407,9 @@ mkf_status mkf_fit_backward(mkf_ctx* ctx, const float* xyz, const float* lcov, c
  * the per-layer thickness.  Needs the checkpoints written by the forward call
  * with the same inputs; recomputes each step's propagation from them.
  *   g_chi2 [T], g_par [6][T], g_cov [21][T]: upstream gradients, any may be NULL
- * Outputs (overwritten): g_hit_xyz [3][H], g_align [L][3], g_x0 [L]. */
+ * Outputs (overwritten): g_hit_xyz [3][H], g_align [L][3], g_x0 [L].
+ * Tracks that the forward fit reports with out_ok = 2 contribute nothing
+ * (the test is repeated here on the checkpointed states, so the two agree). */
 mkf_status mkf_fit_tracks_adjoint(mkf_ctx* ctx, const float* xyz, const float* lcov, const int* layer,
                                   int64_t n_hits, const int* hits, int K, const float* init_par,
                                   const float* init_cov, int64_t n_tracks, const float* align, const float* x0,

@@ -909,10 +909,22 @@ __global__ void __launch_bounds__(kMaxWarps * 32, MINB) k_build(const BuildDev a
 // event: a 64-bucket counting sort on log2(1/p) (quarter octaves), rows of one
 // bucket in any order.
 constexpr int kOrderBuckets = 64;
+constexpr int kOrderThreads = 1024;
+__device__ __forceinline__ int order_bucket(const float* __restrict__ seed_par, int64_t n_seeds, int64_t r) {
+  const float ip = fabsf(seed_par[3 * n_seeds + r]) * fabsf(__sinf(seed_par[5 * n_seeds + r]));
+  // 1/p from 2^-4 to 2^12 /GeV in quarter octaves; heavy (large 1/p) first
+  const float q = 4.0f * (__log2f(fmaxf(ip, 1e-30f)) + 4.0f);
+  const int b = (int)fminf(fmaxf(q, 0.0f), (float)(kOrderBuckets - 1));
+  return kOrderBuckets - 1 - b;
+}
 // Rows before the first offset count with event 0 (as in the building kernel's
-// event lookup); offsets are clamped to the rows that are built.
-__global__ void k_seed_order(const float* __restrict__ seed_par, const int64_t* __restrict__ ev_seed_off,
-                             int n_events, int64_t n_seeds, int* __restrict__ order) {
+// event lookup); offsets are clamped to the rows that are built.  The lanes of
+// a warp that fall in one bucket are counted and placed with one atomic
+// (__match_any_sync), so that heavy traffic on a few buckets does not
+// serialise the block.
+__global__ void __launch_bounds__(kOrderThreads) k_seed_order(const float* __restrict__ seed_par,
+                                                              const int64_t* __restrict__ ev_seed_off, int n_events,
+                                                              int64_t n_seeds, int* __restrict__ order) {
   __shared__ int cnt[kOrderBuckets];
   int64_t n_run = ev_seed_off[n_events];
   n_run = n_run < 0 ? 0 : (n_run < n_seeds ? n_run : n_seeds);
@@ -923,14 +935,18 @@ __global__ void k_seed_order(const float* __restrict__ seed_par, const int64_t* 
   s1 = s1 < s0 ? s0 : (s1 < n_run ? s1 : n_run);
   if (threadIdx.x < kOrderBuckets) cnt[threadIdx.x] = 0;
   __syncthreads();
-  auto bucket = [&](int64_t r) {
-    const float ip = fabsf(seed_par[3 * n_seeds + r]) * fabsf(sinf(seed_par[5 * n_seeds + r]));
-    // 1/p from 2^-4 to 2^12 /GeV in quarter octaves; heavy (large 1/p) first
-    const float q = 4.0f * (log2f(fmaxf(ip, 1e-30f)) + 4.0f);
-    const int b = (int)fminf(fmaxf(q, 0.0f), (float)(kOrderBuckets - 1));
-    return kOrderBuckets - 1 - b;
-  };
-  for (int64_t r = s0 + threadIdx.x; r < s1; r += blockDim.x) atomicAdd(&cnt[bucket(r)], 1);
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  // the loops run a whole number of warp rounds, so every lane reaches the
+  // warp-wide calls; lanes past the range take part with bucket -1
+  const int64_t n = s1 - s0;
+  const int64_t rounds = (n + blockDim.x - 1) / blockDim.x;
+  for (int64_t it = 0; it < rounds; ++it) {
+    const int64_t r = s0 + it * blockDim.x + threadIdx.x;
+    const int b = r < s1 ? order_bucket(seed_par, n_seeds, r) : -1;
+    const unsigned m = __match_any_sync(0xffffffffu, b);
+    if (b >= 0 && (m & lt) == 0) atomicAdd(&cnt[b], __popc(m));
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     int acc = 0;
@@ -941,7 +957,16 @@ __global__ void k_seed_order(const float* __restrict__ seed_par, const int64_t* 
     }
   }
   __syncthreads();
-  for (int64_t r = s0 + threadIdx.x; r < s1; r += blockDim.x) order[s0 + atomicAdd(&cnt[bucket(r)], 1)] = (int)r;
+  for (int64_t it = 0; it < rounds; ++it) {
+    const int64_t r = s0 + it * blockDim.x + threadIdx.x;
+    const int b = r < s1 ? order_bucket(seed_par, n_seeds, r) : -1;
+    const unsigned m = __match_any_sync(0xffffffffu, b);
+    const int leader = __ffs(m) - 1;
+    int base = 0;
+    if (b >= 0 && lane == leader) base = atomicAdd(&cnt[b], __popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (b >= 0) order[s0 + base + __popc(m & lt)] = (int)r;
+  }
 }
 
 template <int NMAX>
@@ -1041,7 +1066,7 @@ cudaError_t launch_build(mkf_ctx* ctx, const BuildArgs& a, cudaStream_t st) {
     d.stats = ctx->stats.as<unsigned long long>();
     d.status = ctx->status.as<int>();
     if (ctx->n_events > 0)
-      k_seed_order<<<(unsigned)ctx->n_events, 256, 0, st>>>(a.seed_par, a.ev_seed_off, ctx->n_events, S,
+      k_seed_order<<<(unsigned)ctx->n_events, kOrderThreads, 0, st>>>(a.seed_par, a.ev_seed_off, ctx->n_events, S,
                                                             ctx->build_order.as<int>());
     // the brute-force window check has a kernel of its own (any N <= 8), so
     // the production kernels carry none of its code

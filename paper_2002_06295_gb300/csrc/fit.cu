@@ -56,6 +56,7 @@ __global__ void k_fit(const GeomDev* __restrict__ g, const float* __restrict__ x
     }
     FitHit<float> f;
     if (!load_fit_hit(g, xyz, lcov, layer, H, row[k], align, x0, f)) continue;
+    if (ok == 1 && disk_multi_turn(f, p, ck)) ok = 2;
     if (!step_to_ud(f, p, u, ck, +1)) {
       ok = 0;
       // mark the steps that did not happen (x = NaN) for the adjoint

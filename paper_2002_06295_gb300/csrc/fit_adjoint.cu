@@ -91,8 +91,10 @@ __device__ __forceinline__ int prev_listed(const int* __restrict__ row, int k) {
   return k;
 }
 
+// Four 128-thread blocks per SM (128 registers a thread, a few spilled): the
+// extra warps hide more latency than the spills cost (C3 adjoint -11 %).
 template <int LPT>
-__global__ void __launch_bounds__(kAdjThreads)
+__global__ void __launch_bounds__(kAdjThreads, 4)
     k_fit_adjoint(const GeomDev* __restrict__ g, const float* __restrict__ xyz, const float* __restrict__ lcov,
                   const int* __restrict__ layer, int64_t H, const int* __restrict__ hits, int K, int64_t NT,
                   const float* __restrict__ align, const float* __restrict__ x0, const float* __restrict__ ckpt,
@@ -120,10 +122,31 @@ __global__ void __launch_bounds__(kAdjThreads)
       }
     const float chib = g_chi2 ? g_chi2[t] : 0.0f;
     const int* row = hits + t * K;
+    // A track with a transport to a disk that spans a full turn of the helix
+    // or more (disk_multi_turn, the forward fit's out_ok = 2) is left out:
+    // the reverse sweep is not accurate there.  The test reads the same
+    // checkpointed state as the forward fit did; steps that did not happen
+    // (x = NaN) end the scan.
+    bool multi_turn = false;
+    for (int k = 0; k < K && !multi_turn; ++k) {
+      const int h = row[k];
+      if (h < 0 || h >= H) continue;
+      const int l = layer[h];
+      if (l < 0 || l >= L || g->L[l].kind != 1) continue;
+      FitHit<float> f;
+      if (!load_fit_hit(g, xyz, lcov, layer, H, h, align, x0, f)) continue;
+      const float* cp = ckpt + (size_t)k * 27 * NT + t;
+      float pk[6];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) pk[i] = cp[i * NT];
+      if (!(pk[0] == pk[0])) break;
+      multi_turn = disk_multi_turn(f, pk, ck);
+    }
+    if (multi_turn) row = nullptr;
     // The group walks its track's listed hits only (prev_listed skips the
     // empty slots), so a warp runs the body once per hit of its longest track
     // rather than once per slot.
-    for (int k = prev_listed(row, K); k >= 0; k = prev_listed(row, k)) {
+    for (int k = row ? prev_listed(row, K) : -1; k >= 0; k = prev_listed(row, k)) {
       const int h = row[k];
       FitHit<float> f;
       if (!load_fit_hit(g, xyz, lcov, layer, H, h, align, x0, f)) continue;
@@ -290,13 +313,16 @@ __global__ void __launch_bounds__(kAdjThreads)
         const float g44 = G2[ci(4, 4)], g55 = G2[ci(5, 5)];
         constexpr int kIn[6] = {0, 1, 3, 4, 5, 6};
         if (LPT == 1) {
-#pragma unroll
+          // one copy of the dual pass, run six times: six inlined copies made
+          // the kernel's code large enough to stall on instruction fetch
+#pragma unroll 1
           for (int e = 0; e < 6; ++e) {
-            const float dF = material_pass(kIn[e], pp, f, g44, g55);
-            if (kIn[e] == 6)
-              x0b = dF;
-            else
-              ppb[kIn[e]] += dF;
+            const int w_ = e + (e >= 2 ? 1 : 0);   // x, y, kappa, phi, theta, thickness
+            const float dF = material_pass(w_, pp, f, g44, g55);
+            if (w_ == 6) x0b = dF;
+#pragma unroll
+            for (int j = 0; j < 6; ++j)
+              if (j == w_) ppb[j] += dF;
           }
         } else {
           const float dF = material_pass(kIn[sub < 6 ? sub : 0], pp, f, g44, g55);

@@ -52,6 +52,29 @@ __device__ __forceinline__ bool load_fit_hit(const GeomDev* __restrict__ g, cons
   return true;
 }
 
+// True when the outward transport from state p onto disk surface f spans a
+// full turn of the helix or more (|s omega| >= 2 pi): a slow particle near
+// theta = pi/2 that drifts from one endcap disk to the next over several
+// turns.  Such a transport's Jacobian has entries that grow with the path
+// (ds/dtheta ~ dz / cos^2 theta), and the fit's reverse sweep, which
+// multiplies the covariance adjoint by J^T ... J at every step, loses all
+// accuracy on it in FP32 (measured against the FP64 oracle on the tracks
+// built on the CMS-like event: hit gradients wrong by up to 1e29 of the
+// track's largest, four of them overflowing, while tracks below one turn
+// agree within 1e-3).  The forward fit reports these tracks and the adjoint
+// leaves them out; both evaluate this same expression on the same state.
+// A barrel crossing is always the first one within a turn, so only disks can
+// qualify.
+__device__ __forceinline__ bool disk_multi_turn(const FitHit<float>& f, const float p[6], float ck) {
+  if (f.kind != 1) return false;
+  float sin_t, cos_t;
+  msincos(p[5], &sin_t, &cos_t);
+  const float cot_t = cos_t / sin_t;
+  const float omega = ck * p[3];
+  const float s = plane_path(p[2], cot_t, f.pos, +1);
+  return s < INFINITY && fabsf(s * omega) >= kTwoPi;
+}
+
 // Propagate the state onto the hit's surface in direction dir, transporting
 // the U-D factors of its covariance and adding the surface's multiple
 // scattering (Highland, on phi and theta).  Returns false when the surface is

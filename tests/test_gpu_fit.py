@@ -100,7 +100,8 @@ def test_fit_cmslike_mixed_surfaces():
     par, cov, chi2, ok = oracle.fit(oracle.Geo.of(g), ev.hit_xyz, ev.hit_lcov, ev.hit_layer, hits, sp, sc)
     gp = o["par"].cpu().numpy().T.astype(np.float64)
     gc = o["cov"].cpu().numpy().T.astype(np.float64)
-    good = ok.astype(bool) & (o["ok"].cpu().numpy() == 1)
+    # ok = 2: fitted, with a transport onto a disk of a full turn or more (no adjoint)
+    good = ok.astype(bool) & (o["ok"].cpu().numpy() >= 1)
     assert good.mean() > 0.99
     pe = par_rel_err(gp[good], par[good])
     worst = np.argmax(pe.max(1))
