@@ -13,7 +13,7 @@ import torch
 
 from . import api
 
-BIN_CHOICES = ((32, 8), (64, 16), (128, 16), (128, 32), (256, 32), (256, 64))
+BIN_CHOICES = ((32, 8), (64, 16), (128, 16), (128, 32), (256, 32), (256, 64), (256, 128))
 WARP_CHOICES = (2, 4, 8)
 
 
