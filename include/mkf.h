@@ -289,9 +289,8 @@ mkf_status mkf_set_build_dedup(mkf_ctx* ctx, int enabled);
 /* Work split of mkf_cluster_strips (TMA path): strips per staged chunk,
  * events per work item (an item is 32 consecutive modules of that many events,
  * whose calibration is staged once per chunk) and pipeline stages per warp.
- * Built splits (chunk, events, stages): (32,1,2) (32,1,3) (32,1,4) (32,2,2)
- * (64,1,2) (64,1,3) (64,2,2); 0, 0, 0 = default: (32,1,2) below 32 events,
- * (32,2,2) from 32 events up.
+ * Built splits (chunk, events, stages): (32,1,1) (32,1,2) (32,1,3) (32,1,4) (32,2,2)
+ * (64,1,2) (64,1,3) (64,2,2); 0, 0, 0 = default: (32,1,1).
  * Speed only: the clusters found are the same (their order in the output is
  * not fixed anyway).  MKF_ERR_ARG for any other triple.  The paper has no
  * counterpart. */

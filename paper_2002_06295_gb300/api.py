@@ -173,7 +173,7 @@ def mkf_set_adjoint_config(ctx, lanes_per_track=0):
     ctx._check(ctx.lib.mkf_set_adjoint_config(ctx.h, int(lanes_per_track)), "mkf_set_adjoint_config")
 
 
-STRIP_SPLITS = ((32, 1, 2), (32, 1, 3), (32, 1, 4), (32, 2, 2), (64, 1, 2), (64, 1, 3), (64, 2, 2))
+STRIP_SPLITS = ((32, 1, 1), (32, 1, 2), (32, 1, 3), (32, 1, 4), (32, 2, 2), (64, 1, 2), (64, 1, 3), (64, 2, 2))
 
 
 def mkf_set_strip_config(ctx, chunk=0, events_per_item=0, stages=0):

@@ -595,9 +595,9 @@ cudaError_t launch_tma(mkf_ctx* ctx, const uint16_t* adc, const uint16_t* noise_
 
 namespace {
 // Work splits the TMA kernel is built for: strips per chunk, events per item, stages.
-constexpr int kStripSplits[][3] = {{32, 1, 2}, {32, 1, 3}, {32, 1, 4}, {32, 2, 2},
+constexpr int kStripSplits[][3] = {{32, 1, 1}, {32, 1, 2}, {32, 1, 3}, {32, 1, 4}, {32, 2, 2},
                                     {64, 1, 2}, {64, 1, 3}, {64, 2, 2}};
-constexpr int kStripDefault[3] = {32, 1, 2};
+constexpr int kStripDefault[3] = {32, 1, 1};
 }  // namespace
 
 extern "C" mkf_status mkf_set_strip_config(mkf_ctx* ctx, int chunk, int events_per_item, int stages) {
@@ -636,12 +636,13 @@ extern "C" mkf_status mkf_cluster_strips(mkf_ctx* ctx, const uint16_t* adc, cons
                    (uintptr_t)bad % 16 == 0;
   if (tma) {
     bool encoded = false;
-    // default: one event per item for small batches (more, shorter items fill
-    // the GPU evenly); two from 32 events up (the calibration is staged once
-    // for both, and there are items enough)
+    // default: one event per item and one stage per warp.  A warp then holds
+    // 5.8 KB of shared memory, so 9 blocks (36 warps) fit an SM, twice the
+    // two-stage split's residency: the other warps' loads hide each warp's
+    // load latency, and the items fill fewer, fuller rounds
     const bool dflt = ctx->strip_chunk == 0;
     const int ch = dflt ? kStripDefault[0] : ctx->strip_chunk,
-              ev = dflt ? (n_events >= 32 ? 2 : kStripDefault[1]) : ctx->strip_events,
+              ev = dflt ? kStripDefault[1] : ctx->strip_events,
               ns = dflt ? kStripDefault[2] : ctx->strip_stages;
 #define MKF_STRIP_ARGS                                                                                           \
   ctx, adc, noise_q, bad, n_events, n_modules, n_strips, max_bad_gap, q_min, out_row, out_first, out_last, \
@@ -650,7 +651,7 @@ extern "C" mkf_status mkf_cluster_strips(mkf_ctx* ctx, const uint16_t* adc, cons
   else if (ch == C && ev == E && ns == S) e = mkf::launch_tma<C, E, S>(MKF_STRIP_ARGS);
     if (false) {
     }
-    MKF_STRIP_CASE(32, 1, 2) MKF_STRIP_CASE(32, 1, 3) MKF_STRIP_CASE(32, 1, 4) MKF_STRIP_CASE(32, 2, 2)
+    MKF_STRIP_CASE(32, 1, 1) MKF_STRIP_CASE(32, 1, 2) MKF_STRIP_CASE(32, 1, 3) MKF_STRIP_CASE(32, 1, 4) MKF_STRIP_CASE(32, 2, 2)
     MKF_STRIP_CASE(64, 1, 2) MKF_STRIP_CASE(64, 1, 3) MKF_STRIP_CASE(64, 2, 2)
     else return ctx->fail(MKF_ERR_ARG, "strip config");
 #undef MKF_STRIP_CASE

@@ -58,7 +58,7 @@ def _run(n_modules, n_strips, n_events, gap, seed, config=(0, 0, 0), max_out=Non
     return ctx, o, n, _oracle(evs, nq, bad, gap, 30)
 
 
-_SPLITS = ((32, 1, 2), (32, 1, 3), (32, 1, 4), (32, 2, 2), (64, 1, 2), (64, 1, 3), (64, 2, 2))
+_SPLITS = ((32, 1, 1), (32, 1, 2), (32, 1, 3), (32, 1, 4), (32, 2, 2), (64, 1, 2), (64, 1, 3), (64, 2, 2))
 
 
 @pytest.mark.parametrize("n_strips,gap,config", [(768, 1, c) for c in _SPLITS] + [
