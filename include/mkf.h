@@ -217,6 +217,13 @@ mkf_status mkf_find_overlaps(mkf_ctx* ctx, const float* xyz, const float* lcov, 
                              float chi2_cut, float max_drphi, float max_dw, int* out_hit, float* out_chi2,
                              void* stream);
 
+/* Launch shape of mkf_find_overlaps: lanes_per_track 1 (one thread per track),
+ * 8 (eight lanes per track run its fit together and share the hits of each
+ * search window), or 0 = by track count (8 below 128 tracks per SM).  Speed
+ * only: the overlap hits and chi2 values are the same in every shape.  The
+ * paper has no counterpart.  MKF_ERR_ARG for any other value. */
+mkf_status mkf_set_overlap_config(mkf_ctx* ctx, int lanes_per_track);
+
 /* Work counters of the last mkf_find_overlaps (synchronises `stream`): [0]
  * track hits fitted, [1] candidate hits whose chi2 was evaluated, [2] overlap
  * hits found.  HOST output of n <= 3 values. */

@@ -8,6 +8,7 @@ from .api import (MkfError, Context, mkf_create, mkf_destroy, mkf_sync, mkf_load
                   mkf_set_adjoint_config,
                   mkf_get_stats, mkf_set_timing, mkf_get_timings, mkf_set_strip_config, mkf_cluster_strips,
                   mkf_seed_tracks, mkf_set_seed_config, mkf_get_seed_stats, mkf_find_overlaps, mkf_get_overlap_stats,
+                  mkf_set_overlap_config,
                   mkf_dedup_tracks, mkf_dedup_tracks_noalloc,
                   mkf_fit_tracks, mkf_fit_backward, mkf_fit_tracks_adjoint, alloc_build_outputs, TRK_SHORT, TRK_KEPT,
                   TRK_DUP)
@@ -18,6 +19,7 @@ __all__ = ["MkfError", "Context", "mkf_create", "mkf_destroy", "mkf_sync", "mkf_
            "mkf_set_adjoint_config",
            "mkf_get_stats", "mkf_set_timing", "mkf_get_timings", "mkf_set_strip_config", "mkf_cluster_strips",
            "mkf_seed_tracks", "mkf_set_seed_config", "mkf_get_seed_stats", "mkf_find_overlaps", "mkf_get_overlap_stats",
+           "mkf_set_overlap_config",
            "mkf_dedup_tracks", "mkf_dedup_tracks_noalloc",
            "mkf_fit_tracks", "mkf_fit_backward", "mkf_fit_tracks_adjoint", "alloc_build_outputs", "TRK_SHORT",
            "TRK_KEPT", "TRK_DUP"]

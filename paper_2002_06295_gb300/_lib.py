@@ -38,6 +38,7 @@ SIGNATURES = {
     "mkf_set_seed_config": (i32, [P, i64]),
     "mkf_find_overlaps": (i32, [P, P, P, P, i64, P, i32, P, P, i64, f32, f32, f32, P, P, P]),
     "mkf_get_overlap_stats": (i32, [P, P, i32, P]),
+    "mkf_set_overlap_config": (i32, [P, i32]),
     "mkf_cluster_strips": (i32, [P, P, P, P, i32, i32, i32, i32, i32, P, P, P, P, P, i64, P, P]),
     "mkf_dedup_tracks": (i32, [P, P, i32, P, P, P, i32, i64, i64, i32, f32, P, P]),
     "mkf_dedup_tracks_noalloc": (i32, [P, i32, P, P, P, i32, i64, i64, i32, f32, P, P, P]),

@@ -298,6 +298,10 @@ def mkf_find_overlaps(ctx, xyz, lcov, layer, hits, init_par, init_cov, chi2_cut=
 OVERLAP_STAT_NAMES = ("hits_fitted", "candidates", "found")
 
 
+def mkf_set_overlap_config(ctx, lanes_per_track=0):
+    ctx._check(ctx.lib.mkf_set_overlap_config(ctx.h, int(lanes_per_track)), "mkf_set_overlap_config")
+
+
 def mkf_get_overlap_stats(ctx, stream=None):
     buf = (ctypes.c_int64 * len(OVERLAP_STAT_NAMES))()
     ctx._check(ctx.lib.mkf_get_overlap_stats(ctx.h, ctypes.cast(buf, ctypes.c_void_p), len(OVERLAP_STAT_NAMES),

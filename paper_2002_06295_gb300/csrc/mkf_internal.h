@@ -69,6 +69,7 @@ struct mkf_ctx {
   int build_group = 0;   // lanes per seed (0: max_cands rounded up to a power of two)
   int build_dedup = 1;   // mkf_build_tracks ends with duplicate removal
   int adjoint_lanes = 0; // lanes per track of the fit adjoint (0: by track count)
+  int overlap_lanes = 0; // lanes per track of the overlap-hit search (0: by track count)
   int strip_chunk = 0;   // strips per staged chunk of the clustering kernel (0: default)
   int strip_events = 0;  // events per clustering work item (0: default)
   int strip_stages = 0;  // pipeline stages per warp of the clustering kernel (0: default)

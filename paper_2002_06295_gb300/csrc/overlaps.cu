@@ -11,7 +11,11 @@
 // (ties: smaller id).  The state is not updated with it, so the fit result
 // does not depend on the search.
 //
-// One thread per track.  The search looks only at the bins of a conservative
+// LPT lanes per track (1, or 8 when there are few tracks): every lane of the
+// group runs the track's fit, the lanes share the hits of the search window,
+// and the best candidate is reduced over the group (smallest chi2, then
+// smallest id), so the result is the same for every LPT.  The search looks
+// only at the bins of a conservative
 // window: around the updated state, half-widths sqrt(cut (C + V_max)) + 5 % in
 // r*phi and in z (barrel) or r (disk), from the state's position covariance
 // and the largest hit variances of the (event, layer) -- the same bound the
@@ -43,7 +47,9 @@ __device__ __forceinline__ HitRec load_hit_rec(const float4* __restrict__ rec, i
   return h;
 }
 
-// The work of one track (t >= NT: none).
+// The work of one track (t >= NT: none), by lane `sub` of its LPT-lane group
+// (group mask gm).
+template <int LPT>
 __device__ __forceinline__ void track_overlaps(const GeomDev* __restrict__ g, const float* __restrict__ xyz,
                                                const float* __restrict__ lcov, const int* __restrict__ layer,
                                                int64_t H, const int* __restrict__ hits, int K,
@@ -53,13 +59,14 @@ __device__ __forceinline__ void track_overlaps(const GeomDev* __restrict__ g, co
                                                const int* __restrict__ bin_off, const float* __restrict__ vmax,
                                                const int64_t* __restrict__ ev_hit_off, int n_events,
                                                int* __restrict__ out_hit, float* __restrict__ out_chi2, int64_t t,
-                                               int& n_fit, int& n_cand, int& n_found) {
+                                               int sub, unsigned gm, int& n_fit, int& n_cand, int& n_found) {
   if (t >= NT) return;
   const int* row = hits + t * K;
-  for (int k = 0; k < K; ++k) {
+  for (int k = sub; k < K; k += LPT) {
     out_hit[t * K + k] = -1;
     out_chi2[t * K + k] = 0.f;
   }
+  if (LPT > 1) __syncwarp(gm);   // the slots are rewritten below by lane 0 of the group
   int first = -1;
   for (int k = 0; k < K && first < 0; ++k) first = row[k] >= 0 && row[k] < H ? row[k] : -1;
   if (first < 0) return;
@@ -87,7 +94,7 @@ __device__ __forceinline__ void track_overlaps(const GeomDev* __restrict__ g, co
     if (!load_fit_hit(g, xyz, lcov, layer, H, h, (const float*)nullptr, (const float*)nullptr, f)) continue;
     if (!step_to_ud(f, p, u, ck, +1)) break;
     ud_update(f.kind, p, u, f.m);
-    ++n_fit;
+    if (sub == 0) ++n_fit;
     // search window around the updated state on the same layer
     const LayerDev ly = g->L[f.layer];
     float cp[6];
@@ -123,7 +130,7 @@ __device__ __forceinline__ void track_overlaps(const GeomDev* __restrict__ g, co
       if (ip < 0) ip += ly.nphi;
       const int b0 = ebase + ly.bin_base + ip * ly.nw;
       const int p0 = __ldg(&bin_off[b0 + iw0]), p1 = __ldg(&bin_off[b0 + iw1 + 1]);
-      for (int pos = p0; pos < p1; ++pos) {
+      for (int pos = p0 + sub; pos < p1; pos += LPT) {
         const HitRec hr = load_hit_rec(rec, pos);
         if (hr.orig == h) continue;
         const float cd = fmaf(f.m.c, hr.c, f.m.s * hr.s), sd = fmaf(f.m.c, hr.s, -f.m.s * hr.c);
@@ -136,7 +143,18 @@ __device__ __forceinline__ void track_overlaps(const GeomDev* __restrict__ g, co
         }
       }
     }
-    if (best_id >= 0 && best < cut) {
+    if (LPT > 1) {
+#pragma unroll
+      for (int o = LPT / 2; o > 0; o >>= 1) {
+        const float ob = __shfl_xor_sync(gm, best, o);
+        const int oi = __shfl_xor_sync(gm, best_id, o);
+        if (ob < best || (ob == best && oi >= 0 && (best_id < 0 || oi < best_id))) {
+          best = ob;
+          best_id = oi;
+        }
+      }
+    }
+    if (sub == 0 && best_id >= 0 && best < cut) {
       out_hit[t * K + k] = best_id;
       out_chi2[t * K + k] = best;
       ++n_found;
@@ -144,6 +162,7 @@ __device__ __forceinline__ void track_overlaps(const GeomDev* __restrict__ g, co
   }
 }
 
+template <int LPT>
 __global__ void __launch_bounds__(kOverlapThreads)
     k_overlaps(const GeomDev* __restrict__ g, const float* __restrict__ xyz, const float* __restrict__ lcov,
                const int* __restrict__ layer, int64_t H, const int* __restrict__ hits, int K,
@@ -152,11 +171,12 @@ __global__ void __launch_bounds__(kOverlapThreads)
                const float* __restrict__ vmax,
                const int64_t* __restrict__ ev_hit_off, int n_events, int* __restrict__ out_hit,
                float* __restrict__ out_chi2, unsigned long long* __restrict__ stats) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / LPT;
+  const int sub = threadIdx.x % LPT;
+  const unsigned gm = LPT == 32 ? 0xFFFFFFFFu : ((1u << LPT) - 1u) << ((threadIdx.x & 31) - sub);
   int n_fit = 0, n_cand = 0, n_found = 0;   // work counters
-  track_overlaps(g, xyz, lcov, layer, H, hits, K, init_par, init_cov, NT, cut, max_drphi, max_dw, rec, bin_off, vmax,
-                 ev_hit_off,
-                 n_events, out_hit, out_chi2, t, n_fit, n_cand, n_found);
+  track_overlaps<LPT>(g, xyz, lcov, layer, H, hits, K, init_par, init_cov, NT, cut, max_drphi, max_dw, rec, bin_off,
+                      vmax, ev_hit_off, n_events, out_hit, out_chi2, t, sub, gm, n_fit, n_cand, n_found);
   const int v[3] = {n_fit, n_cand, n_found};
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -190,18 +210,35 @@ extern "C" mkf_status mkf_find_overlaps(mkf_ctx* ctx, const float* xyz, const fl
   if ((e = ctx->ovl_stats.ensure(4 * sizeof(unsigned long long))) != cudaSuccess) return ctx->fail(MKF_ERR_OOM, "stats");
   if ((e = cudaMemsetAsync(ctx->ovl_stats.p, 0, 4 * sizeof(unsigned long long), st)) != cudaSuccess)
     return ctx->cuda_fail(e, "memset");
-  // one thread per track; small blocks when there are few tracks so that the
-  // work spreads over every SM
-  const int T = n_tracks >= (int64_t)ctx->n_sm * 128 ? 128 : (n_tracks >= (int64_t)ctx->n_sm * 64 ? 64 : 32);
-  const unsigned blocks = (unsigned)((n_tracks + T - 1) / T);
-  k_overlaps<<<blocks, T, 0, st>>>(ctx->geom_dev.as<GeomDev>(), xyz, lcov, layer, n_hits, hits, K,
-                                                  init_par, init_cov, n_tracks, chi2_cut, max_drphi, max_dw,
-                                                  ctx->rec.as<float4>(),
-                                                  ctx->bin_off.as<int>(), ctx->vmax.as<float>(),
-                                                  ctx->ev_hit_off.as<int64_t>(), ctx->n_events, out_hit, out_chi2,
-                                                  ctx->ovl_stats.as<unsigned long long>());
+  // few tracks: eight lanes a track share its search and give the SMs enough
+  // warps; many tracks: one thread a track, in small blocks when there are
+  // not many, so that the work spreads over every SM
+  int lpt = ctx->overlap_lanes;
+  if (lpt != 1 && lpt != 8) lpt = n_tracks < (int64_t)ctx->n_sm * kOverlapThreads ? 8 : 1;
+  if (lpt == 8) {
+    const int64_t threads = n_tracks * 8;
+    k_overlaps<8><<<(unsigned)((threads + kOverlapThreads - 1) / kOverlapThreads), kOverlapThreads, 0, st>>>(
+        ctx->geom_dev.as<GeomDev>(), xyz, lcov, layer, n_hits, hits, K, init_par, init_cov, n_tracks, chi2_cut,
+        max_drphi, max_dw, ctx->rec.as<float4>(), ctx->bin_off.as<int>(), ctx->vmax.as<float>(),
+        ctx->ev_hit_off.as<int64_t>(), ctx->n_events, out_hit, out_chi2, ctx->ovl_stats.as<unsigned long long>());
+  } else {
+    const int T = n_tracks >= (int64_t)ctx->n_sm * 128 ? 128 : (n_tracks >= (int64_t)ctx->n_sm * 64 ? 64 : 32);
+    const unsigned blocks = (unsigned)((n_tracks + T - 1) / T);
+    k_overlaps<1><<<blocks, T, 0, st>>>(ctx->geom_dev.as<GeomDev>(), xyz, lcov, layer, n_hits, hits, K, init_par,
+                                        init_cov, n_tracks, chi2_cut, max_drphi, max_dw, ctx->rec.as<float4>(),
+                                        ctx->bin_off.as<int>(), ctx->vmax.as<float>(), ctx->ev_hit_off.as<int64_t>(),
+                                        ctx->n_events, out_hit, out_chi2, ctx->ovl_stats.as<unsigned long long>());
+  }
   e = cudaGetLastError();
   if (e != cudaSuccess) return ctx->cuda_fail(e, "overlaps");
+  return MKF_OK;
+}
+
+extern "C" mkf_status mkf_set_overlap_config(mkf_ctx* ctx, int lanes_per_track) {
+  if (!ctx) return MKF_ERR_ARG;
+  if (lanes_per_track != 0 && lanes_per_track != 1 && lanes_per_track != 8)
+    return ctx->fail(MKF_ERR_ARG, "lanes_per_track must be 0, 1 or 8");
+  ctx->overlap_lanes = lanes_per_track;
   return MKF_OK;
 }
 

@@ -386,3 +386,29 @@ def test_dedup_split_from_building_on_a_side_stream():
     for k in ("hits", "layers", "counts", "score"):
         assert np.array_equal(out[k].cpu().numpy(), ref[k]), k
     ctx.close()
+
+
+def test_tracks_do_not_depend_on_the_seed_order():
+    """The library builds each event's seeds in an order of its own (most
+    expensive first) and deals the first ones over the blocks; a seed's track
+    must not depend on that.  Seed rows permuted within each event (which
+    changes the building order and the dealing) give bit-identical tracks per
+    seed, on the C2 event and on a small C3 batch.  (Duplicate removal breaks
+    exact score ties by seed index, so its flags are not compared.)"""
+    for cid, ns in ((2, [None]), (3, [300, 40, 900])):
+        evs = [synth.make_config_event(cid, e, n_tracks=n) for e, n in enumerate(ns)]
+        ref = gpu_build(make_ctx(evs[0].geom), evs, max_cands=synth.WORKLOAD_SPECS[cid]["max_cands"])
+        rng = np.random.default_rng(27)
+        perms = []
+        for e in evs:
+            p = rng.permutation(e.n_seeds)
+            perms.append(p)
+            e.seed_par, e.seed_cov = e.seed_par[p], e.seed_cov[p]
+        got = gpu_build(make_ctx(evs[0].geom), evs, max_cands=synth.WORKLOAD_SPECS[cid]["max_cands"])
+        # row j of event e now holds seed perms[e][j]
+        back = np.concatenate([off + p for off, p in zip(ref["seed_off"][:-1], perms)])
+        for k in ("hits", "layers", "counts", "par", "cov", "score", "chi2"):
+            a = got[k] if k != "counts" else got[k].T
+            b = ref[k] if k != "counts" else ref[k].T
+            assert np.array_equal(a, b[back], equal_nan=True) if a.dtype.kind == "f" else np.array_equal(a, b[back]), \
+                (cid, k)

@@ -144,9 +144,9 @@ def test_no_tracks_and_tracks_without_hits(event):
 
 
 def test_same_in_every_launch_shape(event):
-    """One thread per track in blocks of 32, 64 or 128 by track count: copies
-    of the same tracks find the same overlap hits with the same chi2, bit for
-    bit, in every shape."""
+    """One thread per track in blocks of 32, 64 or 128 by track count, and
+    eight lanes per track: copies of the same tracks find the same overlap
+    hits with the same chi2, bit for bit, in every shape."""
     import paper_2002_06295_gb300 as mkf
     from tests._util import f32, i32
     ev = event
@@ -156,15 +156,19 @@ def test_same_in_every_launch_shape(event):
     ctx, d, dev = _setup(ev)
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     outs = {}
-    for copies in (1, (n_sm * 64) // n + 1, (n_sm * 128) // n + 1):
-        o = mkf.mkf_find_overlaps(ctx, d["xyz"], d["lcov"], d["layer"], i32(np.tile(hits, (copies, 1)), dev),
-                                  f32(np.tile(ev.seed_par[sel], (copies, 1)).T, dev),
-                                  f32(np.tile(ev.seed_cov[sel], (copies, 1)).T, dev), chi2_cut=CUT)
-        mkf.mkf_sync(ctx)
-        outs[copies] = (o["hit"].cpu().numpy(), o["chi2"].cpu().numpy())
-    bh, bc = outs[1]
+    for lanes in (1, 8):
+        mkf.mkf_set_overlap_config(ctx, lanes)
+        for copies in (1, (n_sm * 64) // n + 1, (n_sm * 128) // n + 1):
+            o = mkf.mkf_find_overlaps(ctx, d["xyz"], d["lcov"], d["layer"], i32(np.tile(hits, (copies, 1)), dev),
+                                      f32(np.tile(ev.seed_par[sel], (copies, 1)).T, dev),
+                                      f32(np.tile(ev.seed_cov[sel], (copies, 1)).T, dev), chi2_cut=CUT)
+            mkf.mkf_sync(ctx)
+            outs[(lanes, copies)] = (o["hit"].cpu().numpy(), o["chi2"].cpu().numpy())
+    with pytest.raises(mkf.MkfError):
+        mkf.mkf_set_overlap_config(ctx, 4)
+    bh, bc = outs[(1, 1)]
     assert (bh >= 0).sum() > 0
-    for copies, (h, c) in outs.items():
+    for (lanes, copies), (h, c) in outs.items():
         for k in range(copies):
             rows = slice(k * n, (k + 1) * n)
             assert np.array_equal(h[rows], bh), copies
