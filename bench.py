@@ -43,7 +43,7 @@ UNIT = "cand-steps/s"
 # FP32 work per unit, counted from the kernel formulas as executed (FMA = 2,
 # add/mul/div = 1; sqrt, rsqrt, sin/cos, atan, log not counted); barrel-surface
 # counts, so disk-heavy work is under-counted
-FLOPS_NAV_TEST = 44       # one surface tested by the navigation (crossing path + acceptance)
+FLOPS_NAV_TEST = 44       # one surface whose crossing the navigation computed (crossing path + acceptance)
 # one candidate step: helix 46 + Jacobian 84 + material 25 + window ~35 + the
 # U-D transport 676 (J U rows 120, the theta row 17, Gram-Schmidt of rows 4..0
 # 455, position covariance 84)

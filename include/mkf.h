@@ -320,7 +320,8 @@ mkf_status mkf_set_debug(mkf_ctx* ctx, int brute_force_window_check);
 /* Work counters of the last mkf_build_tracks (synchronises `stream`):
  * [0] candidate steps, [1] candidate-hit pairs examined in the search windows
  * (each gets the window box test), [2] hit updates, [3] tracks kept,
- * [4] window violations (debug), [5] navigation surface tests, [6] seeds,
+ * [4] window violations (debug), [5] navigation surface tests whose crossing was
+ * computed, [6] seeds,
  * [7] pairs that passed the box test and had their chi2 computed.
  * HOST output of n <= 8 values. */
 mkf_status mkf_get_stats(mkf_ctx* ctx, int64_t* out, int n, void* stream);
