@@ -54,6 +54,30 @@ FLOPS_CHI2 = 33           # rest of the chi2 of a pair that passes the box test 
 # the hit covariance's decorrelation, rows and residuals (21)
 FLOPS_UPDATE = 301
 FP32_LANES = 128          # per SM (Blackwell)
+# FP32 work per track-hit of the fit gradient (C4), counted the same way: the
+# outward U-D fit step (path 41, helix 46, Jacobian 84, material 25, U-D
+# transport 676, update 301, checkpoint C = U D U^T 189, cot and omega 2), and
+# the adjoint step with its recompute (path, helix, Jacobian 171, plain
+# J C J^T 408, material 27, update quantities 138), the update reverse 718,
+# the transport reverse 846, six material dual passes (~80 each) and seven
+# propagation dual passes (path, helix and Jacobian on dual numbers, an add
+# costing 2, a multiply 4 and an FMA 6 flops: ~3 x 171, plus the contraction
+# 56), and the hit-frame terms 20
+FLOPS_FIT_HIT = 1364
+FLOPS_ADJ_HIT = 6795
+# HBM bytes per track-hit of the fit gradient: the 27-float checkpoint written
+# by the fit and read by the adjoint, the hit's xyz, covariance and layer read
+# by both, its slot of the hit list read by both; per track: seed state read
+# by both, fit outputs written; per hit: its gradient written
+BYTES_FIT_TRACKHIT = 2 * 108 + 2 * 28 + 2 * 4
+BYTES_FIT_TRACK = 2 * 108 + 116
+BYTES_FIT_HIT = 12
+# HBM bytes of the binning stage: per hit, its xyz, covariance and layer read
+# twice (key pass, scatter pass), its key and rank written and read, two
+# 32-byte records written; per bin, the count written and read by the scan
+# and the offset written
+BYTES_BIN_HIT = 2 * 28 + 2 * 8 + 2 * 32
+BYTES_BIN_BIN = 12
 
 
 def parse():
@@ -447,9 +471,19 @@ def measure_fit_gradient(mkf, dev, reps=3):
     mkf.mkf_sync(ctx)
     ctx.close()
     ms = min(ts)
+    n_th = int((hits >= 0).sum())
+    flops = n_th * (FLOPS_FIT_HIT + FLOPS_ADJ_HIT)
+    byts = n_th * BYTES_FIT_TRACKHIT + T * BYTES_FIT_TRACK + ev.n_hits * BYTES_FIT_HIT
+    peak, hbm = fp32_peak(dev), measured_peaks().get("hbm_gbs", 6800.0)
+    achieved = flops / (ms * 1e-3) / 1e12
     return {"workload": "C4: %d tracks x 14 hits, barrel of 14 cylinders; outward fit with checkpoints "
                         "(%.0f MB) + adjoint to hit xyz, alignment, thickness" % (T, K * 27 * T * 4 / 1e6),
-            "ms": ms, "fit_gradient_tracks_per_s": T / (ms * 1e-3)}
+            "ms": ms, "fit_gradient_tracks_per_s": T / (ms * 1e-3),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "algorithmic_flops": flops, "peak_basis": FP32_PEAK_BASIS,
+                         "hbm": {"algorithmic_bytes": byts, "achieved_gbs": byts / (ms * 1e-3) / 1e9,
+                                 "frac": byts / (ms * 1e-3) / 1e9 / hbm,
+                                 "peak_basis": "MEASURED_PEAKS.json hbm_gbs (measured copy)"}}}
 
 
 def measure_strips(mkf, dev, reps=5):
@@ -1005,7 +1039,21 @@ def path_summary(r, workload, dev, max_mhz=None):
                                "cuda_graph": None if r["graph_ms"] is None else r["graph_ms"] / steps,
                                "graph_note": r["graph_note"]},
         "work": st,
+        "binning_roofline": binning_roofline(r),
     }
+
+
+def binning_roofline(r):
+    """HBM roofline of the binning stage (its five kernels) of one step."""
+    tu = r.get("tuned") or {}
+    n_bins = int(r["n_events"]) * int(r["L"]) * int(tu.get("n_phi", 64)) * int(tu.get("n_w", 16))
+    ms = r["stage"]["bin"]
+    byts = r["n_hits"] * BYTES_BIN_HIT + n_bins * BYTES_BIN_BIN
+    hbm = measured_peaks().get("hbm_gbs", 6800.0)
+    gbs = byts / (ms * 1e-3) / 1e9 if ms > 0 else None
+    return {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": None if gbs is None else gbs / hbm,
+            "algorithmic_bytes": byts, "bins": n_bins, "ms": ms,
+            "note": "bins = events x layers x tuned phi x w bins (every layer binned alike)"}
 
 
 def c1_latency(r):
@@ -1107,6 +1155,7 @@ def main():
         "stage_ms": summ["stage_ms"],
         "work": r["stats"],
         "roofline": summ["roofline"],
+        "binning_roofline": summ["binning_roofline"],
         "cpu_baseline": cpu,
         "e2e": summ["e2e"],
         "gpu_launches": summ["gpu_launches"],
