@@ -33,3 +33,18 @@ def test_digest_follows_the_sources():
     a = bench.kernel_digest(bench.KERNEL_SOURCES)
     assert len(a) == 40 and a == bench.kernel_digest(bench.KERNEL_SOURCES)
     assert a != bench.kernel_digest(bench.STRIP_SOURCES)
+
+
+def test_binning_roofline_counts_hits_and_bins(monkeypatch):
+    """Algorithmic bytes of the binning stage: per hit and per bin, with the
+    bins of every layer of every event at the tuned granularity."""
+    monkeypatch.setattr(bench, "measured_peaks", lambda: {"hbm_gbs": 1000.0})
+    r = dict(n_events=4, L=10, n_hits=1000, tuned=dict(n_phi=8, n_w=2), stage=dict(bin=0.5))
+    rl = bench.binning_roofline(r)
+    bins = 4 * 10 * 8 * 2
+    assert rl["bins"] == bins
+    assert rl["algorithmic_bytes"] == 1000 * bench.BYTES_BIN_HIT + bins * bench.BYTES_BIN_BIN
+    assert abs(rl["achieved"] - rl["algorithmic_bytes"] / 0.5e-3 / 1e9) < 1e-9
+    assert abs(rl["frac"] - rl["achieved"] / 1000.0) < 1e-12
+    r["stage"]["bin"] = -1.0   # stage not timed
+    assert bench.binning_roofline(r)["achieved"] is None
