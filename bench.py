@@ -93,7 +93,7 @@ def parse():
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c5"],
                     help="timed workload (c2: the CMS-like event the metric is quoted on)")
     ap.add_argument("--no-graph", action="store_true", help="time eager launches only (no CUDA-graph replay)")
-    ap.add_argument("--only", choices=["strips", "seeding", "overlaps", "in_flight"],
+    ap.add_argument("--only", choices=["strips", "seeding", "overlaps", "in_flight", "fit_gradient"],
                     help="run one secondary measurement alone and print it (for profiling its kernel)")
     return ap.parse_args()
 
@@ -1085,7 +1085,7 @@ def main():
         import paper_2002_06295_gb300 as mkf_only
         dev_only = torch.device("cuda", local)
         fn = {"strips": measure_strips, "seeding": measure_seeding, "overlaps": measure_overlaps,
-              "in_flight": measure_in_flight}[args.only]
+              "in_flight": measure_in_flight, "fit_gradient": measure_fit_gradient}[args.only]
         print(json.dumps({args.only: fn(mkf_only, dev_only)}), flush=True)
         return
     dist = None
