@@ -412,3 +412,14 @@ def test_tracks_do_not_depend_on_the_seed_order():
             b = ref[k] if k != "counts" else ref[k].T
             assert np.array_equal(a, b[back], equal_nan=True) if a.dtype.kind == "f" else np.array_equal(a, b[back]), \
                 (cid, k)
+
+
+def test_dedup_of_the_built_cmslike_event():
+    """Duplicate removal on the 5000 tracks built on the C2 event equals the
+    oracle's greedy rule applied to those tracks, flag for flag."""
+    import oracle
+    ev = synth.make_config_event(2)
+    g = gpu_build(make_ctx(ev.geom), [ev], max_cands=6)
+    exp = oracle.dedup(g["hits"], g["score"].astype(np.float64), g["nhits"], 4, 0.5)
+    assert (g["flags"] == 2).sum() > 100
+    assert np.array_equal(g["flags"], exp)

@@ -133,3 +133,14 @@ def test_full_batch_refit_sampled_tracks(stress):
     print("C5 inward refit: %d tracks, par err" % good.sum(), pe.max(0), "cov err", ce.max())
     assert pe.max() < PAR_RTOL
     assert ce.max() < COV_RTOL
+
+
+def test_full_batch_duplicate_removal(stress):
+    """Duplicate removal on the whole batch (640000 tracks) equals the greedy
+    rule of the oracle applied to the GPU's own tracks: every flag matches.
+    Scores are the GPU's FP32 values on both sides, so ties are the same."""
+    import oracle
+    g, spec = stress["g"], stress["spec"]
+    exp = oracle.dedup(g["hits"], g["score"].astype(np.float64), g["nhits"], spec["min_hits"], spec["dup_frac"])
+    print("flags (short, kept, duplicate):", np.bincount(g["flags"], minlength=3))
+    assert np.array_equal(g["flags"], exp)
