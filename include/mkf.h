@@ -386,7 +386,9 @@ mkf_status mkf_dedup_tracks_noalloc(const int* hits, int L, const float* score, 
  *     reverse sweep is not accurate, so it leaves the track out; 0 a surface
  *     not reached,
  *   ckpt [K][27][T] or NULL: state (6 parameters, 21 covariance) before step k,
- *   needed by mkf_fit_tracks_adjoint. */
+ *   needed by mkf_fit_tracks_adjoint.
+ * A row with no listed hit returns init_par and init_cov unchanged, chi2 0,
+ * ok 1; n_tracks = 0 launches nothing. */
 mkf_status mkf_fit_tracks(mkf_ctx* ctx, const float* xyz, const float* lcov, const int* layer, int64_t n_hits,
                           const int* hits, int K, const float* init_par, const float* init_cov, int64_t n_tracks,
                           const float* align, const float* x0, float* out_par, float* out_cov, float* out_chi2,
@@ -397,7 +399,8 @@ mkf_status mkf_fit_tracks(mkf_ctx* ctx, const float* xyz, const float* lcov, con
  * diagonal (0.01, 0.01, 0.01 cm^2, (0.05 kappa)^2, 0.0025, 0.0025), updates
  * with the outermost hit in place, then propagates inward (negative path) to
  * each earlier hit, adds its material and updates.  Arguments as
- * mkf_fit_tracks (init_cov is ignored; ckpt unsupported, pass NULL).
+ * mkf_fit_tracks (init_cov is ignored; ckpt unsupported, pass NULL).  A row
+ * with no listed hit returns init_par with that reset covariance, chi2 0, ok 1.
  * Arithmetic: FP64 (the multiple-scattering term in FP32); outputs rounded
  * to FP32.  The prior makes the first updates shrink variances by up to 1e5,
  * and on built tracks that carry wrong picks the updates move the state by

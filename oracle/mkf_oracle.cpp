@@ -736,17 +736,19 @@ template <class T> bool fit_forward(const FitInputs<T>& in, const int* ids, int 
 
 // Backward: from the forward result at the outermost hit, covariance reset to
 // 100 x the seed-style diagonal; update with the outermost hit in place, then
-// propagate inward (s < 0) to each earlier hit, add material, update.
+// propagate inward (s < 0) to each earlier hit, add material, update.  A row
+// with no listed hit keeps the starting state with that reset covariance (the
+// caller's covariance is never an input of the backward fit).
 template <class T> bool fit_backward(const FitInputs<T>& in, const int* ids, int K, T p[6], T C[21], T& chi2) {
   chi2 = T(0.0);
-  int last = -1;
-  for (int k = K - 1; k >= 0; --k)
-    if (ids[k] >= 0) { last = k; break; }
-  if (last < 0) return true;
   for (int i = 0; i < 21; ++i) C[i] = T(0.0);
   const double d[6] = {0.01, 0.01, 0.01, -1.0, 0.0025, 0.0025};
   for (int i = 0; i < 6; ++i) C[ci(i, i)] = T(100.0 * d[i]);
   C[ci(3, 3)] = 100.0 * (0.05 * p[3]) * (0.05 * p[3]);
+  int last = -1;
+  for (int k = K - 1; k >= 0; --k)
+    if (ids[k] >= 0) { last = k; break; }
+  if (last < 0) return true;
   {
     Meas<T> m = fit_meas(in, ids[last]);
     chi2 = chi2 + kf_update(p, C, m, true);

@@ -724,3 +724,48 @@ def test_backward_fit_pulls(orc):
     for name, pl in pulls.items():
         assert abs(pl.mean()) < 0.06, (name, pl.mean())
         assert abs(pl.std() - 1) < 0.08, (name, pl.std())
+
+
+def test_fit_skips_empty_slots_and_keeps_empty_rows(orc):
+    """Fitting applies the KF to the hits found (Sec. 1), so an empty slot (-1)
+    is no step: a row with empty slots between its hits fits exactly like the
+    same hits packed together, in both directions.  A row with no hit leaves
+    the start untouched: forward, the given state and covariance; inward, the
+    given state with the reset prior (100 x the seed-style diagonal
+    0.01, 0.01, 0.01 cm^2, (0.05 kappa)^2, 0.0025, 0.0025), chi2 0."""
+    import oracle
+    g = synth.geometry_barrel14()
+    geo = oracle.Geo.of(g)
+    rng = np.random.default_rng(61)
+    ev = synth.simulate_event(g, 200, rng, pt_range=(1.0, 10.0), eta_max=0.8)
+    sel = np.nonzero((ev.true_hits >= 0).sum(1) == 14)[0][:40]
+    packed = ev.true_hits[sel].copy()
+    sp, sc = ev.seed_par[sel], ev.seed_cov[sel]
+    T, K = packed.shape
+    keep = rng.random((T, K)) < 0.6
+    keep[:, 0] = True
+    gappy = np.full((T, 2 * K), -1, np.int32)
+    compact = np.full((T, K), -1, np.int32)
+    for t in range(T):
+        h = packed[t][keep[t]]
+        compact[t, :len(h)] = h
+        slots = np.sort(rng.choice(2 * K, len(h), replace=False))
+        gappy[t, slots] = h
+    fa = orc.fit(geo, ev.hit_xyz, ev.hit_lcov, ev.hit_layer, gappy, sp, sc)
+    fb = orc.fit(geo, ev.hit_xyz, ev.hit_lcov, ev.hit_layer, compact, sp, sc)
+    for x, y in zip(fa, fb):
+        assert np.array_equal(x, y)
+    ba = orc.fit(geo, ev.hit_xyz, ev.hit_lcov, ev.hit_layer, gappy, fa[0], fa[1], direction=-1)
+    bb = orc.fit(geo, ev.hit_xyz, ev.hit_lcov, ev.hit_layer, compact, fa[0], fa[1], direction=-1)
+    for x, y in zip(ba, bb):
+        assert np.array_equal(x, y)
+    empty = np.full((T, K), -1, np.int32)
+    par, cov, chi2, ok = orc.fit(geo, ev.hit_xyz, ev.hit_lcov, ev.hit_layer, empty, sp, sc)
+    assert np.array_equal(par, sp) and np.array_equal(cov, sc) and (chi2 == 0).all() and ok.all()
+    par, cov, chi2, ok = orc.fit(geo, ev.hit_xyz, ev.hit_lcov, ev.hit_layer, empty, sp, sc, direction=-1)
+    assert np.array_equal(par, sp) and (chi2 == 0).all() and ok.all()
+    prior = np.zeros((T, 6, 6))
+    for i, d in enumerate((0.01, 0.01, 0.01, 0.0, 0.0025, 0.0025)):
+        prior[:, i, i] = 100.0 * d
+    prior[:, 3, 3] = 100.0 * (0.05 * sp[:, 3]) ** 2
+    assert np.allclose(oracle.unpack_cov(cov), prior, rtol=1e-15, atol=0)
