@@ -291,17 +291,16 @@ __device__ __forceinline__ bool step_inward(const InwardHit& f, double p[6], dou
   return true;
 }
 
-// Inward fit: covariance reset to 100 x the seed-style diagonal, update with
-// the outermost hit in place, then propagate inward hit by hit (FP64, plain
-// covariance update).
-__global__ void k_fit_inward(const GeomDev* __restrict__ g, const float* __restrict__ xyz,
-                             const float* __restrict__ lcov, const int* __restrict__ layer, int64_t H,
-                             const int* __restrict__ hits, int K, const float* __restrict__ init_par, int64_t NT,
-                             const float* __restrict__ align, const float* __restrict__ x0,
-                             float* __restrict__ out_par, float* __restrict__ out_cov, float* __restrict__ out_chi2,
-                             int* __restrict__ out_ok) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= NT) return;
+// Inward fit of track t: covariance reset to 100 x the seed-style diagonal,
+// update with the outermost hit in place, then propagate inward hit by hit
+// (FP64, plain covariance update).
+__device__ __forceinline__ void fit_inward_track(const GeomDev* __restrict__ g, const float* __restrict__ xyz,
+                                                 const float* __restrict__ lcov, const int* __restrict__ layer,
+                                                 int64_t H, const int* __restrict__ hits, int K,
+                                                 const float* __restrict__ init_par, int64_t NT,
+                                                 const float* __restrict__ align, const float* __restrict__ x0,
+                                                 float* __restrict__ out_par, float* __restrict__ out_cov,
+                                                 float* __restrict__ out_chi2, int* __restrict__ out_ok, int64_t t) {
   const int* row = hits + t * K;
   double p[6], C[21];
 #pragma unroll
@@ -339,7 +338,22 @@ __global__ void k_fit_inward(const GeomDev* __restrict__ g, const float* __restr
   if (out_ok) out_ok[t] = ok;
 }
 
+
+// Inward fit of the tracks t, t + (threads of the grid), ... (the launch caps
+// the grid at two blocks per SM when there are many tracks).
+__global__ void k_fit_inward(const GeomDev* __restrict__ g, const float* __restrict__ xyz,
+                             const float* __restrict__ lcov, const int* __restrict__ layer, int64_t H,
+                             const int* __restrict__ hits, int K, const float* __restrict__ init_par, int64_t NT,
+                             const float* __restrict__ align, const float* __restrict__ x0,
+                             float* __restrict__ out_par, float* __restrict__ out_cov, float* __restrict__ out_chi2,
+                             int* __restrict__ out_ok) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < NT; t += (int64_t)gridDim.x * blockDim.x)
+    fit_inward_track(g, xyz, lcov, layer, H, hits, K, init_par, NT, align, x0, out_par, out_cov, out_chi2, out_ok, t);
+}
+
 }  // namespace
+
+constexpr unsigned kInwardBlocksPerSm = 2;
 
 cudaError_t launch_fit(mkf_ctx* ctx, int direction, const float* xyz, const float* lcov, const int* layer,
                        int64_t n_hits, const int* hits, int K, const float* init_par, const float* init_cov,
@@ -350,7 +364,19 @@ cudaError_t launch_fit(mkf_ctx* ctx, int direction, const float* xyz, const floa
   // work spreads over every SM
   const int T = n_tracks >= (int64_t)ctx->n_sm * 128 ? 128 : (n_tracks >= (int64_t)ctx->n_sm * 64 ? 64 : 32);
   const int tid = direction > 0 ? kTFit : kTBackward;
-  const unsigned grid = (unsigned)((n_tracks + T - 1) / T);
+  unsigned grid = (unsigned)((n_tracks + T - 1) / T);
+  // The inward fit is bound by the FP64 unit of each SM sub-partition (a
+  // warp-wide FP64 instruction holds it for ~67 cycles).  With many tracks,
+  // two 128-thread blocks per SM loop over them: one warp per sub-partition
+  // leaves the unit idle while it waits on loads (the inward fit took twice as
+  // long on a 256-event batch), while three blocks of this 140-register kernel,
+  // as one thread per track would place them, leave no room for a block of
+  // the adjoint that runs beside it on another stream; two leave room for
+  // one (whole step on that batch -1.7 %).
+  if (direction < 0 && T == 128) {
+    const unsigned cap = (unsigned)ctx->n_sm * kInwardBlocksPerSm;
+    if (grid > cap) grid = cap;
+  }
   ctx->tick(tid, st);
   if (direction > 0)
     k_fit<<<grid, T, 0, st>>>(ctx->geom_dev.as<GeomDev>(), xyz, lcov, layer, n_hits, hits, K, init_par,

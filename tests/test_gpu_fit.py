@@ -198,9 +198,10 @@ def test_backward_fit_built_c2_tracks():
 
 def test_backward_fit_same_in_every_launch_shape():
     """The inward fit runs one thread per track in blocks of 32, 64 or 128 by
-    track count (the batched workloads take 128): copies of the same tracks
-    give bit-identical results in every shape, and every copy equals the
-    first."""
+    track count; from 128 threads per SM on, at most two blocks per SM whose
+    threads loop over the tracks (the batched workloads; the last count gives
+    each thread two or three tracks): copies of the same tracks give
+    bit-identical results in every shape, and every copy equals the first."""
     import paper_2002_06295_gb300 as mkf
     g = synth.geometry_cmslike()
     rng = np.random.default_rng(15)
@@ -216,7 +217,7 @@ def test_backward_fit_same_in_every_launch_shape():
     par0 = fo["par"].cpu().numpy().T
     outs = {}
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    for copies in (1, (n_sm * 64) // n + 1, (n_sm * 128) // n + 1):
+    for copies in (1, (n_sm * 64) // n + 1, (n_sm * 128) // n + 1, (n_sm * 640) // n + 1):
         H = np.tile(hits, (copies, 1))
         P = np.tile(par0, (copies, 1))
         o = mkf.mkf_fit_backward(ctx, X, Lc, Ly, i32(H, dev), f32(P.T, dev))
