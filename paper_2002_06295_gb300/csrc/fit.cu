@@ -340,8 +340,9 @@ __device__ __forceinline__ void fit_inward_track(const GeomDev* __restrict__ g, 
 
 
 // Inward fit of the tracks t, t + (threads of the grid), ... (the launch caps
-// the grid at two blocks per SM when there are many tracks).
-__global__ void k_fit_inward(const GeomDev* __restrict__ g, const float* __restrict__ xyz,
+// the grid at two blocks per SM when there are many tracks).  Bounded to 128
+// registers (no spills), so two blocks leave room for two of the adjoint's.
+__global__ void __launch_bounds__(128, 4) k_fit_inward(const GeomDev* __restrict__ g, const float* __restrict__ xyz,
                              const float* __restrict__ lcov, const int* __restrict__ layer, int64_t H,
                              const int* __restrict__ hits, int K, const float* __restrict__ init_par, int64_t NT,
                              const float* __restrict__ align, const float* __restrict__ x0,
@@ -369,10 +370,10 @@ cudaError_t launch_fit(mkf_ctx* ctx, int direction, const float* xyz, const floa
   // warp-wide FP64 instruction holds it for ~67 cycles).  With many tracks,
   // two 128-thread blocks per SM loop over them: one warp per sub-partition
   // leaves the unit idle while it waits on loads (the inward fit took twice as
-  // long on a 256-event batch), while three blocks of this 140-register kernel,
-  // as one thread per track would place them, leave no room for a block of
-  // the adjoint that runs beside it on another stream; two leave room for
-  // one (whole step on that batch -1.7 %).
+  // long on a 256-event batch), while three blocks per SM, as one thread per
+  // track would place them, leave little room for the adjoint that runs beside
+  // it on another stream; two leave room for two of its blocks (whole step on
+  // that batch -2 %, on 64 events of 10000 tracks -2 %).
   if (direction < 0 && T == 128) {
     const unsigned cap = (unsigned)ctx->n_sm * kInwardBlocksPerSm;
     if (grid > cap) grid = cap;
