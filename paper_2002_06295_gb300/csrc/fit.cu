@@ -338,16 +338,15 @@ __device__ __forceinline__ void fit_inward_track(const GeomDev* __restrict__ g, 
   if (out_ok) out_ok[t] = ok;
 }
 
-
 // Inward fit of the tracks t, t + (threads of the grid), ... (the launch caps
 // the grid at two blocks per SM when there are many tracks).  Bounded to 128
 // registers (no spills), so two blocks leave room for two of the adjoint's.
-__global__ void __launch_bounds__(128, 4) k_fit_inward(const GeomDev* __restrict__ g, const float* __restrict__ xyz,
-                             const float* __restrict__ lcov, const int* __restrict__ layer, int64_t H,
-                             const int* __restrict__ hits, int K, const float* __restrict__ init_par, int64_t NT,
-                             const float* __restrict__ align, const float* __restrict__ x0,
-                             float* __restrict__ out_par, float* __restrict__ out_cov, float* __restrict__ out_chi2,
-                             int* __restrict__ out_ok) {
+__global__ void __launch_bounds__(128, 4)
+    k_fit_inward(const GeomDev* __restrict__ g, const float* __restrict__ xyz, const float* __restrict__ lcov,
+                 const int* __restrict__ layer, int64_t H, const int* __restrict__ hits, int K,
+                 const float* __restrict__ init_par, int64_t NT, const float* __restrict__ align,
+                 const float* __restrict__ x0, float* __restrict__ out_par, float* __restrict__ out_cov,
+                 float* __restrict__ out_chi2, int* __restrict__ out_ok) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < NT; t += (int64_t)gridDim.x * blockDim.x)
     fit_inward_track(g, xyz, lcov, layer, H, hits, K, init_par, NT, align, x0, out_par, out_cov, out_chi2, out_ok, t);
 }
@@ -370,10 +369,11 @@ cudaError_t launch_fit(mkf_ctx* ctx, int direction, const float* xyz, const floa
   // warp-wide FP64 instruction holds it for ~67 cycles).  With many tracks,
   // two 128-thread blocks per SM loop over them: one warp per sub-partition
   // leaves the unit idle while it waits on loads (the inward fit took twice as
-  // long on a 256-event batch), while three blocks per SM, as one thread per
-  // track would place them, leave little room for the adjoint that runs beside
-  // it on another stream; two leave room for two of its blocks (whole step on
-  // that batch -2 %, on 64 events of 10000 tracks -2 %).
+  // long on a 256-event batch), while one thread per track fills every SM's
+  // registers (three blocks of the former 140-register kernel, four now) and
+  // leaves little room for the adjoint that runs beside it on another stream;
+  // two leave room for two of its blocks (whole step on that batch -2 %, on 64
+  // events of 10000 tracks -2 %).
   if (direction < 0 && T == 128) {
     const unsigned cap = (unsigned)ctx->n_sm * kInwardBlocksPerSm;
     if (grid > cap) grid = cap;
