@@ -48,3 +48,31 @@ def test_binning_roofline_counts_hits_and_bins(monkeypatch):
     assert abs(rl["frac"] - rl["achieved"] / 1000.0) < 1e-12
     r["stage"]["bin"] = -1.0   # stage not timed
     assert bench.binning_roofline(r)["achieved"] is None
+
+
+def test_packed_buffers_hold_every_tensor_in_place():
+    """The end-to-end leg moves each step's inputs, and the results it reads
+    back, as one buffer each: every tensor becomes a view at a 256-byte
+    aligned offset of that buffer, with its own dtype, shape and values, and
+    writing through a view changes the buffer (so one copy of the buffer
+    moves every tensor)."""
+    import torch
+    src = dict(xyz=torch.arange(30, dtype=torch.float32).reshape(3, 10),
+               layer=torch.tensor([3, 1, 4, 1, 5], dtype=torch.int32),
+               off=torch.tensor([0, 7, 9], dtype=torch.int64),
+               empty=torch.zeros((6, 0), dtype=torch.float32))
+    buf, views = bench.packed(src, "cpu")
+    assert buf.dtype == torch.uint8 and buf.dim() == 1
+    end = 0
+    for k, v in src.items():
+        w = views[k]
+        assert w.dtype == v.dtype and w.shape == v.shape and torch.equal(w, v)
+        if w.numel():
+            off = w.data_ptr() - buf.data_ptr()
+            assert off % 256 == 0 and off >= end
+            end = off + w.numel() * w.element_size()
+    assert end <= buf.numel()
+    views["layer"][2] = 40
+    copy = buf.clone()
+    again = copy[views["layer"].data_ptr() - buf.data_ptr():][:20].view(torch.int32)
+    assert again[2].item() == 40 and torch.equal(views["xyz"], src["xyz"])
